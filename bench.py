@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Block-tree build throughput on GB300.
+
+One step = one complete bt_build of the workload text (prefix fingerprints,
+every level's fingerprint / window-scan / verify / mark / pointer / split pass,
+pruning, rank-select counters, leaf text), i.e. the whole hot path, followed by
+bt_free.  Default workload: the 256 MiB versioned text (4 MiB Zipf(1.1) base
+over 96 symbols, 64 versions with 0.05 % edit runs), tau = 4, leaf_len = 32.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...   # the CPU oracle, as it stands
+
+Prints one JSON line.  `value` is throughput with the text already resident in
+HBM; `e2e` is the same metric through the public C ABI with a host buffer (the
+host->device copy of the text and the device->host read of the serialized tree
+inside the timed region).  With N > 1 (torchrun) every rank builds its own
+replica of the workload: the method has no cross-GPU exchange for a single
+text, so there is no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2512_23314_gb300 import workloads  # noqa: E402
+
+METRIC = "block tree build MB/s"
+UNIT = "MB/s"
+
+WORKLOADS = {
+    "text_versions_256MiB": dict(
+        gen=lambda: workloads.text_versions(), sigma=96, tau=4, leaf=32,
+        desc="256 MiB versioned text: 4 MiB Zipf(1.1) base over 96 symbols, 64 versions "
+             "with 0.05% substitute/insert/delete runs of 1-32 bytes"),
+    "dna_copies_1MiB": dict(
+        gen=lambda: workloads.dna_copies(), sigma=4, tau=2, leaf=16,
+        desc="1 MiB DNA: 64 KiB uniform ACGT seed copied 16 times with 0.1% substitutions"),
+    "dna_genome_2GiB": dict(
+        gen=lambda: workloads.dna_genome(), sigma=5, tau=4, leaf=64,
+        desc="2 GiB DNA: 32 MiB uniform ACGT genome, 64 copies with 0.1% SNPs, "
+             "0.01% indels of 1-50 bases, N runs"),
+}
+DEFAULT_WORKLOAD = "text_versions_256MiB"
+SCAN_SOURCE = os.path.join(ROOT, "paper_2512_23314_gb300", "csrc", "bt_level.cu")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--cpu-sample-mib", type=int, default=8,
+                    help="prefix of the workload the CPU oracle builds per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def source_hash(path: str) -> str:
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str) -> float | None:
+    """DRAM bytes per algorithmic byte from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "window_scan_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except OSError:
+        return None
+    if rec.get("kernel") != kernel or rec.get("source_sha256_16") != source_hash(SCAN_SOURCE):
+        return None
+    return rec.get("dram_bytes_per_alg_byte")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(text: np.ndarray, w: dict, sample_mib: int, steps: int = 1) -> dict:
+    """The oracle as it stands, single-threaded, on a prefix of the workload."""
+    import oracle
+    n = min(len(text), sample_mib << 20)
+    sample = np.ascontiguousarray(text[:n])
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        oracle.build(sample, w["tau"], w["leaf"], prune=True)
+        times.append(time.perf_counter() - t0)
+    sec = statistics.median(times)
+    return {"value": n / sec / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n} bytes ({n >> 20} MiB) of the workload text, prune on, "
+                      f"median of {steps} single-threaded builds"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    w = WORKLOADS[args.workload]
+    text = w["gen"]()
+    n = min(len(text), args.cpu_sample_mib << 20)
+    import oracle
+    sample = np.ascontiguousarray(text[:n])
+    for _ in range(args.warmup):
+        oracle.build(sample, w["tau"], w["leaf"], prune=True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.build(sample, w["tau"], w["leaf"], prune=True)
+    sec = time.perf_counter() - t0
+    value = n * args.steps / sec / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "sigma": w["sigma"], "tau": w["tau"],
+                   "leaf_len": w["leaf"], "prune": True, "sample": f"first {n >> 20} MiB"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"first {n} bytes of the {args.workload} text per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2512_23314_gb300 import bt
+
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    w = WORKLOADS[args.workload]
+    text = w["gen"]()
+    n = len(text)
+    d_text = torch.from_numpy(text).cuda()
+    stream = torch.cuda.current_stream()
+    opts = bt.BuildOptions(prune=True).to_c()[0]
+
+    def step(src):
+        h = bt.bt_build_ex(src, n, w["sigma"], w["tau"], w["leaf"], opts, stream)
+        return h
+
+    for _ in range(max(args.warmup, 0)):
+        bt.bt_free(step(d_text))
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # --- device-resident timed region ---------------------------------
+    sampler = ClockSampler(dev)
+    barrier()
+    sampler.start()
+    time.sleep(0.3)
+    bt.bt_profile_reset()
+    bt.bt_profile_enable(True)
+    launches0 = bt.bt_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        bt.bt_free(step(d_text))
+    e1.record(stream)
+    barrier()
+    launches = bt.bt_launch_count() - launches0
+    bt.bt_profile_enable(False)
+    clocks = sampler.stop()
+    prof = bt.bt_profile_read()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n * args.steps * world / (ms / 1e3) / 1e6
+
+    # --- end to end through the C ABI with host buffers -----------------
+    h = step(d_text)
+    stats = bt.bt_stats(h)
+    blob = bt.bt_export(h)
+    bt.bt_free(h)
+    pinned = torch.from_numpy(text).pin_memory()
+    barrier()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    t_host0 = time.perf_counter()
+    e2.record(stream)
+    d2h = 0
+    for _ in range(args.steps):
+        h = step(pinned)
+        d2h = len(bt.bt_export(h))
+        bt.bt_free(h)
+    e3.record(stream)
+    barrier()
+    e2e_ms = (time.perf_counter() - t_host0) * 1e3
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = n * args.steps * world / (e2e_ms / 1e3) / 1e6
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    scan = prof.get("window_scan", {"launches": 0, "ms": 0.0, "bytes": 0})
+    achieved = scan["bytes"] / (scan["ms"] / 1e3) / 1e9 if scan["ms"] > 0 else None
+    ratio = recorded_traffic("k_scan")
+    per_launch_bytes = scan["bytes"] / max(1, scan["launches"])
+    roofline = {
+        "kernel": "k_scan (window scan)",
+        "bound": "hbm",
+        "achieved": achieved,
+        "peak": hbm if hbm else 6800.0,
+        "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "of fallback",
+        "unit": "GB/s",
+        "frac": (achieved / hbm) if (achieved and hbm) else None,
+        "traffic": (ratio * per_launch_bytes) if ratio is not None else None,
+        "alg_bytes_per_launch": per_launch_bytes,
+        "launches": scan["launches"],
+        "share_of_step": (scan["ms"] / ms) if ms > 0 else None,
+    }
+    cov = sum(s["cov"] for s in stats)
+    vbytes = sum(s["verify_bytes"] for s in stats)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "sigma": w["sigma"], "tau": w["tau"],
+                   "leaf_len": w["leaf"], "prune": True, "levels": len(stats),
+                   "sum_cov_bytes": cov, "verify_bytes": vbytes,
+                   "l2": "input (n bytes) larger than the 129 MB L2; no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "kernels_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(text, w, args.cpu_sample_mib)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

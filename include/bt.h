@@ -1,0 +1,179 @@
+/*
+ * bt.h -- C ABI of the GB300 block-tree library (libbt.so).
+ *
+ * A block tree (Belazzougui et al.; the paper's section 3, "Block Trees") is a
+ * compressed index of a text T[0, n) that answers access, rank and select
+ * (the paper's section 1).  bt_build runs the per-level Karp-Rabin pass of
+ * sections 3.1 and 4 on the GPU: fingerprints of every block and of every
+ * pair of consecutive blocks, a scan of every window of the level against
+ * them to find leftmost occurrences, byte verification of every accepted
+ * fingerprint match, marking, back-pointers with offsets, the optional
+ * pruning pass, and the split of surviving blocks into the next level.
+ *
+ * Conventions for every entry point:
+ *  - Positions are 0-based.  The paper's access(i), rank_c(i) (inclusive,
+ *    1-based) and select_c(j) (1-based) map to bt_access(i-1),
+ *    bt_rank(c, i) and bt_select(c, j) + 1.
+ *  - Return value: 0 (BT_OK) or a positive bt_status code; outputs are
+ *    written only on BT_OK.  bt_strerror names a code.
+ *  - Pointers named d_* are device pointers (cudaMalloc'd memory of the
+ *    current device); `text` may be a host or a device pointer (detected with
+ *    cudaPointerGetAttributes).  The caller keeps ownership of every buffer
+ *    it passes; the library owns a bt_tree until bt_free.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the per-thread
+ *    default stream.  Entry points that return host values synchronize it.
+ *  - A built tree is immutable: queries on one tree may run concurrently
+ *    from several host threads.  bt_free must not race with queries.
+ *  - Limits: 1 <= n < 2^32, 2 <= tau <= 64, leaf_len >= 1.
+ *  - There is no CPU fallback: without a usable CUDA device every entry
+ *    point that computes returns BT_ECUDA.
+ */
+#ifndef BT_H
+#define BT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BT_OK = 0,
+  BT_EINVAL = 1,    /* bad argument: n = 0, tau < 2, leaf_len = 0, more distinct
+                       byte values than sigma, bad opts or level sizes       */
+  BT_ERANGE = 2,    /* query out of range; export buffer too small            */
+  BT_ENOMEM = 3,    /* device or host allocation failed                       */
+  BT_ECUDA = 4,     /* a CUDA call failed (no device, launch error, ...)      */
+  BT_ETIMEOUT = 5,  /* a bounded device-side loop gave up                     */
+  BT_EINTERNAL = 6  /* a device-side invariant check failed                   */
+} bt_status;
+
+typedef struct bt_tree bt_tree;
+
+/* Build options.  Initialise with bt_opts_default. */
+typedef struct {
+  int prune;                   /* 1 (default): run the pruning post-pass of
+                                  section 3.1 ("Optional Pruning")            */
+  uint32_t root_arity;         /* 0 (default): the height h is the smallest
+                                  with tau*leaf_len*tau^h >= n; otherwise the
+                                  smallest with root_arity*leaf_len*tau^h >= n */
+  uint64_t seed;               /* selects the Karp-Rabin base B (section 2)   */
+  uint64_t modulus;            /* 0 (default): q = 2^61-1.  Test hook: any q in
+                                  [300, 2^32) makes fingerprint collisions
+                                  frequent; the result must not change.       */
+  const uint64_t* level_sizes; /* host array of explicit block sizes, level 1
+                                  first, each >= 2x and a multiple of the
+                                  next; NULL (default) derives them.          */
+  uint32_t nlevels;            /* entries of level_sizes                      */
+  uint64_t max_rounds;         /* bound on device-side fixed-point rounds
+                                  (pruning); 0 = default 4096.  Exceeding it
+                                  returns BT_ETIMEOUT.                        */
+} bt_opts;
+
+void bt_opts_default(bt_opts* opts);
+
+/*
+ * Build the block tree of text[0, n) (section 3; per-level pass of sections
+ * 3.1 and 4).  sigma is the alphabet size: the text may hold at most sigma
+ * distinct byte values (any values; they need not be < sigma).  tau is the
+ * arity of inner nodes, leaf_len the block length of the last level.
+ * Equivalent to bt_build_ex with bt_opts_default and a NULL stream.
+ * On success *out holds a new tree; on failure *out is NULL.
+ */
+int bt_build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau,
+             uint32_t leaf_len, bt_tree** out);
+
+int bt_build_ex(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau,
+                uint32_t leaf_len, const bt_opts* opts, void* stream, bt_tree** out);
+
+/* access(i) = T[i], 0 <= i < n (section 1).  BT_ERANGE if i >= n. */
+int bt_access(const bt_tree* t, uint64_t i, uint8_t* out);
+
+/* rank_c(i) = number of j < i with T[j] = c, 0 <= i <= n (section 1).
+ * A byte absent from T has rank 0.  BT_ERANGE if i > n. */
+int bt_rank(const bt_tree* t, uint8_t c, uint64_t i, uint64_t* out);
+
+/* select_c(j) = 0-based position of the j-th occurrence of c, j >= 1
+ * (section 1).  BT_ERANGE if j = 0 or j > rank_c(n). */
+int bt_select(const bt_tree* t, uint8_t c, uint64_t j, uint64_t* out);
+
+/* Batched queries on device arrays, asynchronous on `stream`.
+ *   kind BT_Q_ACCESS: d_args[q] = i;                 d_out[q] = T[i]
+ *   kind BT_Q_RANK:   d_args[2q] = c, d_args[2q+1] = i; d_out[q] = rank_c(i)
+ *   kind BT_Q_SELECT: d_args[2q] = c, d_args[2q+1] = j; d_out[q] = select_c(j)
+ * A query out of range writes UINT64_MAX to d_out[q].  Returns BT_EINVAL for a
+ * bad kind, BT_ECUDA if the launch fails. */
+enum { BT_Q_ACCESS = 0, BT_Q_RANK = 1, BT_Q_SELECT = 2 };
+int bt_query_batch(const bt_tree* t, int kind, const uint64_t* d_args, uint64_t m,
+                   uint64_t* d_out, void* stream);
+
+/*
+ * Canonical serialization of the tree (all u64, little-endian):
+ *   "BLKTREE1", n, tau, leaf_len, L, prune;
+ *   per level: nblocks, b, ceil(nblocks/64) words of marks (bit k of word
+ *   k/64 = block k is marked), nptr, then (ptr, off) of every unmarked block
+ *   in block order;
+ *   leaf_bytes, the text of the marked last-level blocks in order, zero
+ *   padded to a multiple of 8.
+ * With buf == NULL (or cap too small) *len receives the size needed; a too
+ * small buffer returns BT_ERANGE.
+ */
+int bt_export(const bt_tree* t, uint8_t* buf, uint64_t cap, uint64_t* len);
+
+/* Number of levels of a built tree. */
+uint32_t bt_levels(const bt_tree* t);
+
+/* Per-level statistics of the construction, BT_ST_FIELDS u64 per level:
+ * blocks, block size, covered bytes (sum of block lengths), marked blocks,
+ * pairs, bytes read by verification, fingerprint collisions found by
+ * verification, blocks after pruning.  cap is in u64 units. */
+enum { BT_ST_NBLOCKS = 0, BT_ST_B, BT_ST_COV, BT_ST_NMARKED, BT_ST_NPAIRS,
+       BT_ST_VERIFY_BYTES, BT_ST_COLLISIONS, BT_ST_FINAL_BLOCKS, BT_ST_FIELDS };
+int bt_stats(const bt_tree* t, uint64_t* out, uint64_t cap);
+
+/*
+ * Karp-Rabin prefix fingerprints (section 2; the data-parallel form of
+ * section 4.1): d_out[j] = H(j*stride) for j = 0 .. n/stride, where
+ * H(0) = 0 and H(p+1) = H(p)*B + T[p] + 1 mod q, with the base B that
+ * bt_build uses for `seed` and q = 2^61-1 (modulus 0) or the given test
+ * modulus.  d_text and d_out are device pointers; d_out holds n/stride + 1
+ * entries.  stride must be 32.  Asynchronous on `stream`.
+ */
+int bt_prefix_fingerprints(const uint8_t* d_text, uint64_t n, uint64_t seed, uint64_t modulus,
+                           uint32_t stride, uint64_t* d_out, void* stream);
+
+/* The base B selected by seed for modulus (0 = 2^61-1). */
+uint64_t bt_fingerprint_base(uint64_t seed, uint64_t modulus);
+
+void bt_free(bt_tree* t);
+
+const char* bt_strerror(int status);
+
+/*
+ * Measurement hooks (not part of the paper's method).  When enabled, the
+ * library records a pair of CUDA events on the launching stream around the
+ * window-scan, prefix-fingerprint, verification and counter kernels of every
+ * build.  bt_profile_read aggregates, per kernel name: launches, total
+ * milliseconds between the events, and the algorithmic bytes those launches
+ * process (the covered bytes of the level for the window scan, n for the
+ * prefix fingerprints, the compared bytes for verification).  It waits for
+ * the recorded events.  Profiling state is process-wide; reads and resets
+ * must not race with builds that record.
+ */
+typedef struct {
+  char name[32];
+  uint64_t launches;
+  double ms;
+  uint64_t bytes;
+} bt_profile_entry;
+void bt_profile_enable(int on);
+void bt_profile_reset(void);
+int bt_profile_read(bt_profile_entry* out, uint32_t cap, uint32_t* count);
+
+/* Number of kernels this library has launched in the process so far. */
+uint64_t bt_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

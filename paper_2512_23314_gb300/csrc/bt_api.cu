@@ -1,0 +1,409 @@
+// bt_api.cu -- the C ABI (include/bt.h) and the host side of a build.
+//
+// bt_build_ex: validate -> text on the device (H2D copy for host input) ->
+// alphabet histogram -> Karp-Rabin prefix fingerprints -> the level loop of
+// bt_level.cu (one device->host read of the next level's size per level) ->
+// pruning (bt_prune.cu) -> counters and leaf text (bt_query.cu).  Every step
+// runs in this library's kernels; the host only sizes buffers and launches.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "bt_internal.cuh"
+
+namespace bt {
+
+int alphabet(const uint8_t* T, uint64_t n, uint32_t sigma, bt_tree* t, cudaStream_t s);
+int upload_view(bt_tree* t, cudaStream_t s);
+int run_queries(const bt_tree* t, int kind, const uint64_t* d_args, uint64_t m, uint64_t* d_out,
+                cudaStream_t s);
+
+void note_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  if (getenv("BT_VERBOSE"))
+    fprintf(stderr, "bt: %s failed at %s:%d: %s\n", what, file, line, cudaGetErrorString(e));
+}
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+struct ProfRec {
+  std::string name;
+  cudaEvent_t a, b;
+  uint64_t bytes;
+};
+std::mutex g_prof_mu;
+std::vector<ProfRec> g_prof;
+std::atomic<int> g_prof_on{0};
+}  // namespace
+
+ProfScope::ProfScope(const char* name, cudaStream_t st, uint64_t bytes) : s(st) {
+  if (!g_prof_on.load()) return;
+  ProfRec r{name, nullptr, nullptr, bytes};
+  if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return;
+  cudaEventRecord(r.a, s);
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  slot = (int)g_prof.size();
+  g_prof.push_back(r);
+}
+
+ProfScope::~ProfScope() {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  cudaEventRecord(g_prof[slot].b, s);
+}
+
+int sync_status(BuildCtx& ctx) {
+  BT_CUDA(cudaMemcpyAsync(ctx.st_host, ctx.st, sizeof(Status), cudaMemcpyDeviceToHost, ctx.s));
+  BT_CUDA(cudaStreamSynchronize(ctx.s));
+  return BT_OK;
+}
+
+// splitmix64 (Steele, Lea, Flood 2014): the seed -> base map.
+static uint64_t splitmix(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+static uint64_t base_for(uint64_t seed, uint64_t q) { return splitmix(seed) % (q - 256) + 256; }
+
+// Block sizes: b_L = leaf_len, b_l = tau * b_{l+1}, height the smallest h
+// with s0 * leaf_len * tau^h >= n (section 3 assumes n = s * tau^h).
+static int plan_sizes(uint64_t n, uint32_t tau, uint32_t leaf, const bt_opts& o,
+                      std::vector<uint64_t>& b) {
+  b.clear();
+  if (o.level_sizes) {
+    if (o.nlevels == 0 || o.nlevels > kMaxLevels) return BT_EINVAL;
+    for (uint32_t l = 0; l < o.nlevels; l++) {
+      uint64_t x = o.level_sizes[l];
+      if (x == 0) return BT_EINVAL;
+      if (l + 1 < o.nlevels) {
+        uint64_t y = o.level_sizes[l + 1];
+        if (y == 0 || x < 2 * y || x % y) return BT_EINVAL;
+      }
+      b.push_back(x);
+    }
+    return BT_OK;
+  }
+  unsigned __int128 size = (unsigned __int128)(o.root_arity ? o.root_arity : tau) * leaf;
+  uint32_t h = 0;
+  while (size < n) {
+    size *= tau;
+    if (++h >= (uint32_t)kMaxLevels) return BT_EINVAL;
+  }
+  b.resize(h + 1);
+  b[h] = leaf;
+  for (int l = (int)h - 1; l >= 0; l--) b[l] = b[l + 1] * tau;
+  return BT_OK;
+}
+
+static void free_tree_memory(bt_tree* t) {
+  for (Level& v : t->lv) {
+    cudaFree(v.st);
+    cudaFree(v.mw);
+    cudaFree(v.mr);
+    cudaFree(v.ptr);
+    cudaFree(v.off);
+    cudaFree(v.lo);
+    cudaFree(v.cnt);
+    cudaFree(v.pc);
+  }
+  cudaFree(t->leaf);
+  cudaFree(t->pre);
+  cudaFree(t->sym);
+  cudaFree(t->view);
+}
+
+static int build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, uint32_t leaf,
+                 const bt_opts& o, cudaStream_t s, bt_tree* t) {
+  std::vector<uint64_t> sizes;
+  BT_TRY(plan_sizes(n, tau, leaf, o, sizes));
+  t->n = n;
+  t->tau = tau;
+  t->leaf_len = leaf;
+  t->L = (uint32_t)sizes.size();
+  t->prune = o.prune ? 1 : 0;
+  t->seed = o.seed;
+  t->q = o.modulus ? o.modulus : Mersenne61::Q;
+  t->B = base_for(o.seed, t->q);
+  t->lv.resize(t->L);
+  for (uint32_t l = 0; l < t->L; l++) t->lv[l].b = sizes[l];
+
+  BT_CUDA(cudaGetDevice(&t->device));
+  Scratch sc(s);
+  // Text on the device.
+  cudaPointerAttributes pa;
+  const uint8_t* dT = text;
+  if (cudaPointerGetAttributes(&pa, text) != cudaSuccess || pa.type == cudaMemoryTypeHost ||
+      pa.type == cudaMemoryTypeUnregistered) {
+    cudaGetLastError();
+    uint8_t* copy;
+    BT_TRY(sc.alloc(&copy, n + 16));
+    BT_CUDA(cudaMemcpyAsync(copy, text, n, cudaMemcpyHostToDevice, s));
+    dT = copy;
+  }
+  BuildCtx ctx;
+  ctx.t = t;
+  ctx.T = dT;
+  ctx.s = s;
+  BT_TRY(sc.alloc(&ctx.st, 1));
+  BT_CUDA(cudaMemsetAsync(ctx.st, 0, sizeof(Status), s));
+  BT_CUDA(cudaMallocHost(&ctx.st_host, sizeof(Status)));
+  struct HostFree {
+    void* p;
+    ~HostFree() { cudaFreeHost(p); }
+  } hf{ctx.st_host};
+
+  BT_TRY(alphabet(dT, n, sigma, t, s));
+  BT_TRY(sc.alloc(&ctx.Hs, n / kPrefixStride + 2));
+  BT_TRY(prefix_fingerprints(dT, n, t->B, t->q, ctx.Hs, s));
+  BT_TRY(build_levels(ctx));
+  if (t->prune) BT_TRY(prune_tree(ctx, o.max_rounds));
+  else
+    for (Level& v : t->lv) v.stats[BT_ST_FINAL_BLOCKS] = v.c;
+  BT_TRY(build_counters(ctx));
+  for (Level& v : t->lv) {
+    cudaFreeAsync(v.lo, s);
+    v.lo = nullptr;
+  }
+  BT_TRY(upload_view(t, s));
+  BT_CUDA(cudaStreamSynchronize(s));
+  BT_TRY(sync_status(ctx));
+  if (ctx.st_host->error) return BT_EINTERNAL;
+  return BT_OK;
+}
+
+static cudaStream_t as_stream(void* s) { return s ? (cudaStream_t)s : cudaStreamPerThread; }
+
+}  // namespace bt
+
+using namespace bt;
+
+extern "C" {
+
+void bt_opts_default(bt_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->prune = 1;
+}
+
+int bt_build_ex(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, uint32_t leaf_len,
+                const bt_opts* opts, void* stream, bt_tree** out) {
+  if (!out) return BT_EINVAL;
+  *out = nullptr;
+  if (!text || n == 0 || n >= (1ull << 32) || tau < 2 || tau > 64 || leaf_len == 0 || sigma == 0)
+    return BT_EINVAL;
+  bt_opts o;
+  if (opts) o = *opts;
+  else bt_opts_default(&o);
+  if (o.modulus && (o.modulus < 300 || o.modulus >= (1ull << 32))) return BT_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return BT_ECUDA;
+  }
+  bt_tree* t = new (std::nothrow) bt_tree();
+  if (!t) return BT_ENOMEM;
+  int rc = build(text, n, sigma, tau, leaf_len, o, as_stream(stream), t);
+  if (rc != BT_OK) {
+    cudaStreamSynchronize(as_stream(stream));
+    free_tree_memory(t);
+    delete t;
+    return rc;
+  }
+  *out = t;
+  return BT_OK;
+}
+
+int bt_build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, uint32_t leaf_len,
+             bt_tree** out) {
+  return bt_build_ex(text, n, sigma, tau, leaf_len, nullptr, nullptr, out);
+}
+
+void bt_free(bt_tree* t) {
+  if (!t) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(t->device);
+  free_tree_memory(t);
+  cudaSetDevice(cur);
+  delete t;
+}
+
+static int single_query(const bt_tree* t, int kind, uint64_t a0, uint64_t a1, uint64_t* res) {
+  if (!t) return BT_EINVAL;
+  cudaStream_t s = cudaStreamPerThread;
+  uint64_t* d;
+  BT_CUDA(cudaMallocAsync(&d, 3 * sizeof(uint64_t), s));
+  uint64_t h[2] = {a0, a1};
+  int rc = BT_OK;
+  if (cudaMemcpyAsync(d, h, sizeof(h), cudaMemcpyHostToDevice, s) != cudaSuccess) rc = BT_ECUDA;
+  if (rc == BT_OK) rc = run_queries(t, kind, d, 1, d + 2, s);
+  if (rc == BT_OK && cudaMemcpyAsync(res, d + 2, sizeof(uint64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    rc = BT_ECUDA;
+  cudaFreeAsync(d, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess && rc == BT_OK) rc = BT_ECUDA;
+  return rc;
+}
+
+int bt_access(const bt_tree* t, uint64_t i, uint8_t* out) {
+  if (!t || !out) return BT_EINVAL;
+  if (i >= t->n) return BT_ERANGE;
+  uint64_t r;
+  BT_TRY(single_query(t, BT_Q_ACCESS, i, 0, &r));
+  if (r == kNone) return BT_EINTERNAL;
+  *out = (uint8_t)r;
+  return BT_OK;
+}
+
+int bt_rank(const bt_tree* t, uint8_t c, uint64_t i, uint64_t* out) {
+  if (!t || !out) return BT_EINVAL;
+  if (i > t->n) return BT_ERANGE;
+  uint64_t r;
+  BT_TRY(single_query(t, BT_Q_RANK, c, i, &r));
+  if (r == kNone) return BT_EINTERNAL;
+  *out = r;
+  return BT_OK;
+}
+
+int bt_select(const bt_tree* t, uint8_t c, uint64_t j, uint64_t* out) {
+  if (!t || !out) return BT_EINVAL;
+  if (j == 0) return BT_ERANGE;
+  uint64_t r;
+  BT_TRY(single_query(t, BT_Q_SELECT, c, j, &r));
+  if (r == kNone) return BT_ERANGE;
+  *out = r;
+  return BT_OK;
+}
+
+int bt_query_batch(const bt_tree* t, int kind, const uint64_t* d_args, uint64_t m, uint64_t* d_out,
+                   void* stream) {
+  if (!t || (m && (!d_args || !d_out))) return BT_EINVAL;
+  if (kind != BT_Q_ACCESS && kind != BT_Q_RANK && kind != BT_Q_SELECT) return BT_EINVAL;
+  return run_queries(t, kind, d_args, m, d_out, as_stream(stream));
+}
+
+uint32_t bt_levels(const bt_tree* t) { return t ? t->L : 0; }
+
+int bt_stats(const bt_tree* t, uint64_t* out, uint64_t cap) {
+  if (!t || !out || cap < (uint64_t)t->L * BT_ST_FIELDS) return BT_EINVAL;
+  for (uint32_t l = 0; l < t->L; l++)
+    memcpy(out + l * BT_ST_FIELDS, t->lv[l].stats, sizeof(uint64_t) * BT_ST_FIELDS);
+  return BT_OK;
+}
+
+int bt_export(const bt_tree* t, uint8_t* buf, uint64_t cap, uint64_t* len) {
+  if (!t || !len) return BT_EINVAL;
+  cudaStream_t s = cudaStreamPerThread;
+  std::vector<uint64_t> out = {0x31454552544B4C42ull, t->n, t->tau, t->leaf_len, t->L,
+                               (uint64_t)t->prune};
+  for (uint32_t l = 0; l < t->L; l++) {
+    const Level& v = t->lv[l];
+    const uint64_t words = (v.c + 31) / 32;
+    std::vector<uint32_t> mw(words), ptr(v.c);
+    std::vector<uint64_t> off(v.c);
+    BT_CUDA(cudaMemcpyAsync(mw.data(), v.mw, words * 4, cudaMemcpyDeviceToHost, s));
+    BT_CUDA(cudaMemcpyAsync(ptr.data(), v.ptr, v.c * 4, cudaMemcpyDeviceToHost, s));
+    BT_CUDA(cudaMemcpyAsync(off.data(), v.off, v.c * 8, cudaMemcpyDeviceToHost, s));
+    BT_CUDA(cudaStreamSynchronize(s));
+    out.push_back(v.c);
+    out.push_back(v.b);
+    for (uint64_t w = 0; w < (v.c + 63) / 64; w++) {
+      uint64_t lo = mw[2 * w], hi = 2 * w + 1 < words ? mw[2 * w + 1] : 0;
+      out.push_back(lo | (hi << 32));
+    }
+    uint64_t nptr = 0;
+    for (uint64_t k = 0; k < v.c; k++) nptr += !((mw[k >> 5] >> (k & 31)) & 1u);
+    out.push_back(nptr);
+    for (uint64_t k = 0; k < v.c; k++) {
+      if ((mw[k >> 5] >> (k & 31)) & 1u) continue;
+      out.push_back(ptr[k]);
+      out.push_back(off[k]);
+    }
+  }
+  out.push_back(t->leaf_bytes);
+  std::vector<uint8_t> leaf((t->leaf_bytes + 7) / 8 * 8, 0);
+  if (t->leaf_bytes) {
+    BT_CUDA(cudaMemcpyAsync(leaf.data(), t->leaf, t->leaf_bytes, cudaMemcpyDeviceToHost, s));
+    BT_CUDA(cudaStreamSynchronize(s));
+  }
+  uint64_t need = out.size() * 8 + leaf.size();
+  *len = need;
+  if (!buf) return BT_OK;
+  if (cap < need) return BT_ERANGE;
+  memcpy(buf, out.data(), out.size() * 8);
+  if (!leaf.empty()) memcpy(buf + out.size() * 8, leaf.data(), leaf.size());
+  return BT_OK;
+}
+
+int bt_prefix_fingerprints(const uint8_t* d_text, uint64_t n, uint64_t seed, uint64_t modulus,
+                           uint32_t stride, uint64_t* d_out, void* stream) {
+  if (!d_text || !d_out || stride != kPrefixStride) return BT_EINVAL;
+  if (modulus && (modulus < 300 || modulus >= (1ull << 32))) return BT_EINVAL;
+  uint64_t q = modulus ? modulus : Mersenne61::Q;
+  return prefix_fingerprints(d_text, n, base_for(seed, q), q, d_out, as_stream(stream));
+}
+
+uint64_t bt_fingerprint_base(uint64_t seed, uint64_t modulus) {
+  return base_for(seed, modulus ? modulus : Mersenne61::Q);
+}
+
+void bt_profile_enable(int on) { g_prof_on.store(on ? 1 : 0); }
+
+void bt_profile_reset(void) {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  for (ProfRec& r : g_prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g_prof.clear();
+}
+
+int bt_profile_read(bt_profile_entry* out, uint32_t cap, uint32_t* count) {
+  if (!count) return BT_EINVAL;
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  std::vector<bt_profile_entry> agg;
+  for (ProfRec& r : g_prof) {
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return BT_ECUDA;
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) return BT_ECUDA;
+    bt_profile_entry* e = nullptr;
+    for (auto& x : agg)
+      if (r.name == x.name) e = &x;
+    if (!e) {
+      agg.push_back(bt_profile_entry{});
+      e = &agg.back();
+      snprintf(e->name, sizeof(e->name), "%s", r.name.c_str());
+    }
+    e->launches++;
+    e->ms += ms;
+    e->bytes += r.bytes;
+  }
+  *count = (uint32_t)agg.size();
+  if (out)
+    for (uint32_t i = 0; i < agg.size() && i < cap; i++) out[i] = agg[i];
+  return BT_OK;
+}
+
+uint64_t bt_launch_count(void) { return g_launches.load(); }
+
+const char* bt_strerror(int status) {
+  switch (status) {
+    case BT_OK: return "ok";
+    case BT_EINVAL: return "invalid argument";
+    case BT_ERANGE: return "out of range";
+    case BT_ENOMEM: return "out of memory";
+    case BT_ECUDA: return "CUDA error";
+    case BT_ETIMEOUT: return "device-side loop bound exceeded";
+    case BT_EINTERNAL: return "internal invariant violated";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,380 @@
+// bt_query.cu -- alphabet map, rank/select counters, leaf text and queries.
+//
+// access, rank and select are the queries of section 1; the paper's
+// implementation stores one bit vector per level plus pointers and offsets
+// (section 4.4) and names the rank/select auxiliary data as future work
+// (section 6).  The counters used here:
+//   cnt[k][s]  occurrences of symbol s in block k (every level),
+//   pc[u][s]   occurrences of s in T[st[ptr], st[ptr] + off) for an unmarked
+//              block u (the part of its target before the copied window),
+//   pre[k][s]  occurrences of s before level-1 block k.
+// rank_c(i) descends from the level-1 block holding i: inside a marked block
+// it adds the counts of the children left of the one holding i; at an
+// unmarked block it continues in its target (ptr or ptr+1) and subtracts
+// pc.  select mirrors it.  One thread answers one query.
+#include "bt_internal.cuh"
+
+namespace bt {
+
+namespace {
+
+__global__ void k_histogram(const uint8_t* __restrict__ T, uint64_t n, unsigned long long* hist) {
+  __shared__ unsigned int h[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  const uint64_t nv = n / 16;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (((uintptr_t)T & 15) == 0) {
+    const uint4* V = (const uint4*)T;
+    for (uint64_t i = tid; i < nv; i += stride) {
+      uint4 q = V[i];
+      uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++) atomicAdd(&h[(w[a] >> (8 * b)) & 0xFF], 1u);
+    }
+    for (uint64_t i = nv * 16 + tid; i < n; i += stride) atomicAdd(&h[T[i]], 1u);
+  } else {
+    for (uint64_t i = tid; i < n; i += stride) atomicAdd(&h[T[i]], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
+}
+
+struct CountJob {
+  const uint64_t* st;   // block starts of the level
+  const uint32_t* ptr;  // for pc jobs: targets
+  const uint64_t* off;
+  const uint32_t* mw;
+  uint64_t c, b, n;
+  uint32_t* out;        // rows of S counters
+  int mode;             // 0: count the block itself, 1: count T[st[ptr], st[ptr]+off)
+  int only_unmarked;    // skip marked blocks
+  int only_marked;
+};
+
+constexpr uint64_t kCountPiece = 1 << 16;
+
+// One warp per (block, piece of at most 64 KiB); symbol counts are gathered
+// in a per-warp shared histogram and added to the block's row.
+__global__ void __launch_bounds__(256) k_count(CountJob J, const int16_t* __restrict__ sym,
+                                               const uint8_t* __restrict__ T, uint32_t S,
+                                               uint64_t ppb) {
+  extern __shared__ unsigned int hist[];  // 8 warps x S
+  const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned int* h = hist + wid * S;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+  for (uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; w < J.c * ppb; w += warps) {
+    const uint64_t k = w / ppb, piece = w - k * ppb;
+    const bool mk = (J.mw[k >> 5] >> (k & 31)) & 1u;
+    if ((J.only_unmarked && mk) || (J.only_marked && !mk)) continue;
+    uint64_t s0, len;
+    if (J.mode == 0) {
+      s0 = J.st[k];
+      len = J.n - s0 < J.b ? J.n - s0 : J.b;
+    } else {
+      s0 = J.st[J.ptr[k]];
+      len = J.off[k];
+    }
+    const uint64_t a = piece * kCountPiece;
+    if (a >= len) continue;
+    const uint64_t e = a + kCountPiece < len ? a + kCountPiece : len;
+    for (uint32_t i = lane; i < S; i += 32) h[i] = 0;
+    __syncwarp();
+    for (uint64_t x = a + lane; x < e; x += 32) atomicAdd(&h[sym[T[s0 + x]]], 1u);
+    __syncwarp();
+    for (uint32_t i = lane; i < S; i += 32)
+      if (h[i]) atomicAdd(&J.out[k * S + i], h[i]);
+    __syncwarp();
+  }
+}
+
+// Marked blocks of a non-last level: sum of the children's counts.
+__global__ void k_sum_children(uint64_t c, uint64_t b, uint64_t n, const uint64_t* __restrict__ st,
+                               const uint32_t* __restrict__ mw, const uint32_t* __restrict__ mr,
+                               uint32_t arity, uint64_t bn, const uint32_t* __restrict__ child_cnt,
+                               uint32_t S, uint32_t* __restrict__ cnt) {
+  for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < c * S;
+       w += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t k = w / S, s = w - k * S;
+    if (!((mw[k >> 5] >> (k & 31)) & 1u)) continue;
+    uint64_t len = n - st[k] < b ? n - st[k] : b;
+    uint64_t first = (mr[k >> 5] + __popc(mw[k >> 5] & ((1u << (k & 31)) - 1u))) * (uint64_t)arity;
+    uint64_t nch = (len + bn - 1) / bn;
+    uint32_t acc = 0;
+    for (uint64_t i = 0; i < nch; i++) acc += child_cnt[(first + i) * S + s];
+    cnt[k * S + s] = acc;
+  }
+}
+
+__global__ void k_level1_prefix(uint64_t c, const uint32_t* __restrict__ cnt, uint32_t S,
+                                uint64_t* __restrict__ pre) {
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
+    uint64_t acc = 0;
+    for (uint64_t k = 0; k < c; k++) {
+      pre[k * S + s] = acc;
+      acc += cnt[k * S + s];
+    }
+    pre[c * S + s] = acc;
+  }
+}
+
+__global__ void k_leaf_text(uint64_t c, uint64_t b, uint64_t n, const uint64_t* __restrict__ st,
+                            const uint32_t* __restrict__ mw, const uint32_t* __restrict__ mr,
+                            const uint8_t* __restrict__ T, uint8_t* __restrict__ leaf) {
+  for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < c * b;
+       w += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t k = w / b, i = w - k * b;
+    if (!((mw[k >> 5] >> (k & 31)) & 1u)) continue;
+    if (st[k] + i >= n) continue;
+    uint64_t r = mr[k >> 5] + __popc(mw[k >> 5] & ((1u << (k & 31)) - 1u));
+    leaf[r * b + i] = T[st[k] + i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Queries.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool qmarked(const LevelView& v, uint64_t k) {
+  return (v.mw[k >> 5] >> (k & 31)) & 1u;
+}
+__device__ __forceinline__ uint64_t qrank(const LevelView& v, uint64_t k) {
+  return v.mr[k >> 5] + __popc(v.mw[k >> 5] & ((1u << (k & 31)) - 1u));
+}
+__device__ __forceinline__ uint64_t qlen(const TreeView& t, const LevelView& v, uint64_t k) {
+  uint64_t s = v.st[k];
+  return t.n - s < v.b ? t.n - s : v.b;
+}
+
+__device__ uint64_t q_access(const TreeView& t, uint64_t i) {
+  if (i >= t.n) return kNone;
+  uint32_t l = 0;
+  uint64_t k = i / t.lv[0].b, x = i;
+  for (uint32_t step = 0; step < 4 * t.L + 4; step++) {
+    const LevelView& v = t.lv[l];
+    if (qmarked(v, k)) {
+      if (l + 1 == t.L) return t.leaf[qrank(v, k) * v.b + (x - v.st[k])];
+      k = qrank(v, k) * v.arity + (x - v.st[k]) / t.lv[l + 1].b;
+      l++;
+    } else {
+      uint64_t P = v.ptr[k];
+      x = v.st[P] + v.off[k] + (x - v.st[k]);
+      k = x < v.st[P] + qlen(t, v, P) ? P : P + 1;
+    }
+  }
+  return kNone;
+}
+
+__device__ uint64_t q_rank(const TreeView& t, uint32_t c, uint64_t i) {
+  if (i > t.n) return kNone;
+  int s = t.sym[c & 0xFF];
+  if (s < 0) return 0;
+  const uint32_t S = t.S;
+  const LevelView& r = t.lv[0];
+  if (i == t.n) return t.pre[r.c * S + s];
+  uint64_t k = i / r.b, o = i - r.st[k];
+  int64_t acc = (int64_t)t.pre[k * S + s];
+  uint32_t l = 0;
+  for (uint32_t step = 0; step < 4 * t.L + 4; step++) {
+    const LevelView& v = t.lv[l];
+    if (o == 0) return (uint64_t)acc;
+    uint64_t len = qlen(t, v, k);
+    if (o == len) return (uint64_t)(acc + v.cnt[k * S + s]);
+    if (qmarked(v, k)) {
+      if (l + 1 == t.L) {
+        const uint8_t* p = t.leaf + qrank(v, k) * v.b;
+        for (uint64_t x = 0; x < o; x++) acc += p[x] == (c & 0xFF);
+        return (uint64_t)acc;
+      }
+      const LevelView& w = t.lv[l + 1];
+      uint64_t j = o / w.b, f = qrank(v, k) * v.arity;
+      for (uint64_t x = 0; x < j; x++) acc += w.cnt[(f + x) * S + s];
+      o -= j * w.b;
+      k = f + j;
+      l++;
+    } else {
+      uint64_t P = v.ptr[k], x = v.off[k] + o;
+      acc -= v.pc[k * S + s];
+      uint64_t lp = qlen(t, v, P);
+      if (x <= lp) {
+        k = P;
+        o = x;
+      } else {
+        acc += v.cnt[P * S + s];
+        k = P + 1;
+        o = x - lp;
+      }
+    }
+  }
+  return kNone;
+}
+
+__device__ uint64_t q_select(const TreeView& t, uint32_t c, uint64_t j) {
+  int s = t.sym[c & 0xFF];
+  if (s < 0 || j == 0) return kNone;
+  const uint32_t S = t.S;
+  const LevelView& r = t.lv[0];
+  if (j > t.pre[r.c * S + s]) return kNone;
+  uint64_t a = 0, z = r.c;  // last k with pre[k] < j
+  while (z - a > 1) {
+    uint64_t mid = (a + z) / 2;
+    if (t.pre[mid * S + s] < j) a = mid;
+    else z = mid;
+  }
+  uint64_t k = a;
+  j -= t.pre[k * S + s];
+  int64_t res = (int64_t)r.st[k];
+  uint32_t l = 0;
+  for (uint32_t step = 0; step < 4 * t.L + 4; step++) {
+    const LevelView& v = t.lv[l];
+    if (qmarked(v, k)) {
+      if (l + 1 == t.L) {
+        const uint8_t* p = t.leaf + qrank(v, k) * v.b;
+        uint64_t len = qlen(t, v, k);
+        for (uint64_t x = 0; x < len; x++)
+          if (p[x] == (c & 0xFF) && --j == 0) return (uint64_t)(res + (int64_t)x);
+        return kNone;
+      }
+      const LevelView& w = t.lv[l + 1];
+      uint64_t f = qrank(v, k) * v.arity, i = 0;
+      while (i < v.arity && w.cnt[(f + i) * S + s] < j) {
+        j -= w.cnt[(f + i) * S + s];
+        i++;
+      }
+      if (i == v.arity) return kNone;
+      res += (int64_t)(i * w.b);
+      k = f + i;
+      l++;
+    } else {
+      uint64_t P = v.ptr[k], jj = j + v.pc[k * S + s];
+      if (jj <= v.cnt[P * S + s]) {
+        res -= (int64_t)v.off[k];
+        k = P;
+        j = jj;
+      } else {
+        res += (int64_t)(qlen(t, v, P) - v.off[k]);
+        j = jj - v.cnt[P * S + s];
+        k = P + 1;
+      }
+    }
+  }
+  return kNone;
+}
+
+__global__ void k_queries(const TreeView* __restrict__ tv, int kind, const uint64_t* __restrict__ args,
+                          uint64_t m, uint64_t* __restrict__ out) {
+  const TreeView& t = *tv;
+  for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < m;
+       q += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t r;
+    if (kind == BT_Q_ACCESS) r = q_access(t, args[q]);
+    else if (kind == BT_Q_RANK) r = args[2 * q] > 255 ? kNone : q_rank(t, (uint32_t)args[2 * q], args[2 * q + 1]);
+    else r = args[2 * q] > 255 ? kNone : q_select(t, (uint32_t)args[2 * q], args[2 * q + 1]);
+    out[q] = r;
+  }
+}
+
+}  // namespace
+
+int alphabet(const uint8_t* T, uint64_t n, uint32_t sigma, bt_tree* t, cudaStream_t s) {
+  Scratch sc(s);
+  unsigned long long* hist;
+  BT_TRY(sc.alloc(&hist, 256));
+  BT_CUDA(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned long long), s));
+  BT_LAUNCH(k_histogram<<<grid_for(n / 16 + 1, 256, 152 * 8), 256, 0, s>>>(T, n, hist));
+  unsigned long long h[256];
+  BT_CUDA(cudaMemcpyAsync(h, hist, sizeof(h), cudaMemcpyDeviceToHost, s));
+  BT_CUDA(cudaStreamSynchronize(s));
+  uint32_t S = 0;
+  for (int i = 0; i < 256; i++) t->sym_host[i] = h[i] ? (int16_t)S++ : (int16_t)-1;
+  if (S > sigma) return BT_EINVAL;
+  t->S = S;
+  BT_CUDA(cudaMalloc(&t->sym, 256 * sizeof(int16_t)));
+  BT_CUDA(cudaMemcpyAsync(t->sym, t->sym_host, 256 * sizeof(int16_t), cudaMemcpyHostToDevice, s));
+  BT_CUDA(cudaStreamSynchronize(s));
+  return BT_OK;
+}
+
+int build_counters(BuildCtx& ctx) {
+  bt_tree* t = ctx.t;
+  cudaStream_t s = ctx.s;
+  const uint32_t S = t->S;
+  const unsigned T = 256;
+  const size_t smem = 8 * S * sizeof(unsigned int);
+  for (int l = (int)t->L - 1; l >= 0; l--) {
+    Level& v = t->lv[l];
+    BT_CUDA(cudaMallocAsync(&v.cnt, v.c * S * sizeof(uint32_t) + 4, s));
+    BT_CUDA(cudaMallocAsync(&v.pc, v.c * S * sizeof(uint32_t) + 4, s));
+    BT_CUDA(cudaMemsetAsync(v.cnt, 0, v.c * S * sizeof(uint32_t), s));
+    BT_CUDA(cudaMemsetAsync(v.pc, 0, v.c * S * sizeof(uint32_t), s));
+    const uint64_t ppb = (v.b + kCountPiece - 1) / kCountPiece;
+    const bool last = l + 1 == (int)t->L;
+    CountJob J{v.st, v.ptr, v.off, v.mw, v.c, v.b, t->n, v.cnt, 0, 0, 0};
+    if (!last) {
+      const Level& w = t->lv[l + 1];
+      BT_LAUNCH(k_sum_children<<<grid_for(v.c * S, T), T, 0, s>>>(v.c, v.b, t->n, v.st, v.mw, v.mr, v.arity, w.b,
+                                                        w.cnt, S, v.cnt));
+      J.only_unmarked = 1;  // marked blocks are sums of their children
+    }
+    BT_LAUNCH(k_count<<<grid_for(v.c * ppb * 32, T), T, smem, s>>>(J, t->sym, ctx.T, S, ppb));
+    CountJob P{v.st, v.ptr, v.off, v.mw, v.c, v.b, t->n, v.pc, 1, 1, 0};
+    BT_LAUNCH(k_count<<<grid_for(v.c * ppb * 32, T), T, smem, s>>>(P, t->sym, ctx.T, S, ppb));
+    BT_CUDA(cudaGetLastError());
+  }
+  const Level& r = t->lv[0];
+  BT_CUDA(cudaMallocAsync(&t->pre, (r.c + 1) * S * sizeof(uint64_t) + 8, s));
+  BT_LAUNCH(k_level1_prefix<<<1, 256, 0, s>>>(r.c, r.cnt, S, t->pre));
+  // Leaf text of the marked last-level blocks.
+  const Level& z = t->lv[t->L - 1];
+  uint32_t nm = 0;
+  BT_CUDA(cudaMemcpyAsync(&nm, z.mr + (z.c + 31) / 32, sizeof(nm), cudaMemcpyDeviceToHost, s));
+  BT_CUDA(cudaStreamSynchronize(s));
+  t->leaf_bytes = (uint64_t)nm * z.b;
+  BT_CUDA(cudaMallocAsync(&t->leaf, t->leaf_bytes + 16, s));
+  BT_LAUNCH(k_leaf_text<<<grid_for(z.c * z.b, T), T, 0, s>>>(z.c, z.b, t->n, z.st, z.mw, z.mr, ctx.T, t->leaf));
+  BT_CUDA(cudaGetLastError());
+  // Real leaf length: the tail block may be short.
+  uint64_t tail_short = 0;
+  if (nm) {
+    uint64_t last_st = 0;
+    BT_CUDA(cudaMemcpyAsync(&last_st, z.st + z.c - 1, sizeof(last_st), cudaMemcpyDeviceToHost, s));
+    uint32_t lastw = 0;
+    BT_CUDA(cudaMemcpyAsync(&lastw, z.mw + (z.c - 1) / 32, sizeof(lastw), cudaMemcpyDeviceToHost, s));
+    BT_CUDA(cudaStreamSynchronize(s));
+    bool last_marked = (lastw >> ((z.c - 1) & 31)) & 1u;
+    if (last_marked && t->n - last_st < z.b) tail_short = z.b - (t->n - last_st);
+  }
+  t->leaf_bytes -= tail_short;
+  return BT_OK;
+}
+
+int upload_view(bt_tree* t, cudaStream_t s) {
+  TreeView h;
+  h.n = t->n;
+  h.L = t->L;
+  h.S = t->S;
+  for (uint32_t l = 0; l < t->L; l++) {
+    const Level& v = t->lv[l];
+    h.lv[l] = LevelView{v.c, v.b, v.arity, v.st, v.mw, v.mr, v.ptr, v.off, v.cnt, v.pc};
+  }
+  h.pre = t->pre;
+  h.leaf = t->leaf;
+  h.sym = t->sym;
+  BT_CUDA(cudaMalloc(&t->view, sizeof(TreeView)));
+  BT_CUDA(cudaMemcpyAsync(t->view, &h, sizeof(TreeView), cudaMemcpyHostToDevice, s));
+  BT_CUDA(cudaStreamSynchronize(s));
+  return BT_OK;
+}
+
+int run_queries(const bt_tree* t, int kind, const uint64_t* d_args, uint64_t m, uint64_t* d_out,
+                cudaStream_t s) {
+  if (m == 0) return BT_OK;
+  BT_LAUNCH(k_queries<<<grid_for(m, 128, 152 * 64), 128, 0, s>>>(t->view, kind, d_args, m, d_out));
+  BT_CUDA(cudaGetLastError());
+  return BT_OK;
+}
+
+}  // namespace bt
