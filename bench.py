@@ -45,6 +45,9 @@ WORKLOADS = {
         gen=lambda: workloads.text_versions(), sigma=96, tau=4, leaf=32,
         desc="256 MiB versioned text: 4 MiB Zipf(1.1) base over 96 symbols, 64 versions "
              "with 0.05% substitute/insert/delete runs of 1-32 bytes"),
+    "text_versions_160MiB": dict(
+        gen=lambda: workloads.text_versions(n=160 << 20), sigma=96, tau=4, leaf=32,
+        desc="160 MiB prefix of the versioned-text workload (profiling captures)"),
     "dna_copies_1MiB": dict(
         gen=lambda: workloads.dna_copies(), sigma=4, tau=2, leaf=16,
         desc="1 MiB DNA: 64 KiB uniform ACGT seed copied 16 times with 0.1% substitutions"),
@@ -148,6 +151,22 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
                 "reasons": sorted(reasons)}
+
+
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """Maximum of a per-rank scalar (timings are taken as the slowest rank)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput_mbs(n_bytes: int, steps: int, world: int, ms: float) -> float:
+    """Whole-job MB/s: every rank builds `steps` replicas of an n-byte text."""
+    return n_bytes * steps * world / (ms / 1e3) / 1e6
 
 
 def dist_setup(args):
@@ -254,12 +273,8 @@ def run_ours(args):
     bt.bt_profile_enable(False)
     clocks = sampler.stop()
     prof = bt.bt_profile_read()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = n * args.steps * world / (ms / 1e3) / 1e6
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    value = throughput_mbs(n, args.steps, world, ms)
 
     # --- end to end through the C ABI with host buffers -----------------
     h = step(d_text)
@@ -279,12 +294,8 @@ def run_ours(args):
         bt.bt_free(h)
     e3.record(stream)
     barrier()
-    e2e_ms = (time.perf_counter() - t_host0) * 1e3
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = n * args.steps * world / (e2e_ms / 1e3) / 1e6
+    e2e_ms = max_over_ranks((time.perf_counter() - t_host0) * 1e3, world)
+    e2e_value = throughput_mbs(n, args.steps, world, e2e_ms)
 
     if rank != 0:
         if world > 1:
@@ -312,13 +323,16 @@ def run_ours(args):
     }
     cov = sum(s["cov"] for s in stats)
     vbytes = sum(s["verify_bytes"] for s in stats)
+    cands = sum(s["candidates"] for s in stats)
+    hits = sum(s["hits"] for s in stats)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": args.workload, "n": n, "sigma": w["sigma"], "tau": w["tau"],
                    "leaf_len": w["leaf"], "prune": True, "levels": len(stats),
-                   "sum_cov_bytes": cov, "verify_bytes": vbytes,
+                   "sum_cov_bytes": cov, "verify_bytes": vbytes, "scan_candidates": cands,
+                   "scan_hits": hits,
                    "l2": "input (n bytes) larger than the 129 MB L2; no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roofline,

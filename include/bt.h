@@ -65,10 +65,15 @@ typedef struct {
                                   first, each >= 2x and a multiple of the
                                   next; NULL (default) derives them.          */
   uint32_t nlevels;            /* entries of level_sizes                      */
-  uint64_t max_rounds;         /* bound on device-side fixed-point rounds
-                                  (pruning); 0 = default 4096.  Exceeding it
-                                  returns BT_ETIMEOUT.                        */
+  uint64_t max_rounds;         /* pruning: parallel frontier rounds before a
+                                  single-thread right-to-left finish of the
+                                  rest; 0 = default 4096.                     */
+  uint32_t flags;              /* BT_FLAG_* (0 by default)                    */
 } bt_opts;
+
+/* flags: probe the table at every window position instead of the anchored
+ * scan (a diagnostic; both give the same tree). */
+enum { BT_FLAG_DENSE_SCAN = 1 };
 
 void bt_opts_default(bt_opts* opts);
 
@@ -126,9 +131,11 @@ uint32_t bt_levels(const bt_tree* t);
 /* Per-level statistics of the construction, BT_ST_FIELDS u64 per level:
  * blocks, block size, covered bytes (sum of block lengths), marked blocks,
  * pairs, bytes read by verification, fingerprint collisions found by
- * verification, blocks after pruning.  cap is in u64 units. */
+ * verification, blocks after pruning, windows the anchored scan proposed,
+ * proposed windows whose fingerprint belongs to a key.  cap is in u64 units. */
 enum { BT_ST_NBLOCKS = 0, BT_ST_B, BT_ST_COV, BT_ST_NMARKED, BT_ST_NPAIRS,
-       BT_ST_VERIFY_BYTES, BT_ST_COLLISIONS, BT_ST_FINAL_BLOCKS, BT_ST_FIELDS };
+       BT_ST_VERIFY_BYTES, BT_ST_COLLISIONS, BT_ST_FINAL_BLOCKS, BT_ST_CANDIDATES,
+       BT_ST_HITS, BT_ST_FIELDS };
 int bt_stats(const bt_tree* t, uint64_t* out, uint64_t cap);
 
 /*

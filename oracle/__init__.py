@@ -209,7 +209,9 @@ class Parsed:
     leaf_text: bytes
 
 
-def parse(blob: bytes) -> Parsed:
+def parse(blob: bytes, as_numpy: bool = False) -> Parsed:
+    """Read the canonical serialization.  With as_numpy, marks are a numpy
+    bool array and ptrs an (nptr, 2) int64 array (fast for large trees)."""
     a = np.frombuffer(blob, dtype="<u8")
     if int(a[0]) != 0x31454552544B4C42:
         raise ValueError("bad magic")
@@ -220,14 +222,17 @@ def parse(blob: bytes) -> Parsed:
         c, b = int(a[i]), int(a[i + 1])
         i += 2
         nw = (c + 63) // 64
-        words = a[i:i + nw]
+        words = np.ascontiguousarray(a[i:i + nw])
         i += nw
-        marks = [(int(words[k // 64]) >> (k % 64)) & 1 for k in range(c)]
+        bits = np.unpackbits(words.view(np.uint8), bitorder="little")[:c].astype(bool)
         nptr = int(a[i])
         i += 1
-        pa = a[i:i + 2 * nptr].reshape(-1, 2)
+        pa = a[i:i + 2 * nptr].reshape(-1, 2).astype(np.int64)
         i += 2 * nptr
-        levels.append(Level(b, marks, [(int(p), int(o)) for p, o in pa]))
+        if as_numpy:
+            levels.append(Level(b, bits, pa))
+        else:
+            levels.append(Level(b, [int(x) for x in bits], [(int(p), int(o)) for p, o in pa]))
     nleaf = int(a[i])
     i += 1
     leaf_text = blob[8 * i:8 * i + nleaf]

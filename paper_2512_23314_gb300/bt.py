@@ -19,9 +19,10 @@ LIBPATH = os.path.join(_HERE, "_lib", "libbt.so")
 
 BT_OK, BT_EINVAL, BT_ERANGE, BT_ENOMEM, BT_ECUDA, BT_ETIMEOUT, BT_EINTERNAL = range(7)
 BT_Q_ACCESS, BT_Q_RANK, BT_Q_SELECT = 0, 1, 2
-ST_FIELDS = 8
+BT_FLAG_DENSE_SCAN = 1
+ST_FIELDS = 10
 ST_NAMES = ("nblocks", "b", "cov", "nmarked", "npairs", "verify_bytes", "collisions",
-            "final_blocks")
+            "final_blocks", "candidates", "hits")
 
 
 class BTError(RuntimeError):
@@ -34,7 +35,7 @@ class bt_opts(ctypes.Structure):
     _fields_ = [("prune", ctypes.c_int), ("root_arity", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("modulus", ctypes.c_uint64),
                 ("level_sizes", ctypes.c_void_p), ("nlevels", ctypes.c_uint32),
-                ("max_rounds", ctypes.c_uint64)]
+                ("max_rounds", ctypes.c_uint64), ("flags", ctypes.c_uint32)]
 
 
 _lib = None
@@ -242,6 +243,7 @@ class BuildOptions:
     modulus: int = 0
     level_sizes: tuple | None = None
     max_rounds: int = 0
+    dense_scan: bool = False
 
     def to_c(self):
         o = bt_opts_default()
@@ -250,6 +252,7 @@ class BuildOptions:
         o.seed = self.seed
         o.modulus = self.modulus
         o.max_rounds = self.max_rounds
+        o.flags = BT_FLAG_DENSE_SCAN if self.dense_scan else 0
         keep = None
         if self.level_sizes is not None:
             keep = np.ascontiguousarray(self.level_sizes, dtype=np.uint64)

@@ -152,6 +152,7 @@ static int build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, 
   ctx.t = t;
   ctx.T = dT;
   ctx.s = s;
+  ctx.dense_scan = (o.flags & BT_FLAG_DENSE_SCAN) ? 1 : 0;
   BT_TRY(sc.alloc(&ctx.st, 1));
   BT_CUDA(cudaMemsetAsync(ctx.st, 0, sizeof(Status), s));
   BT_CUDA(cudaMallocHost(&ctx.st_host, sizeof(Status)));
@@ -162,6 +163,15 @@ static int build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, 
 
   BT_TRY(alphabet(dT, n, sigma, t, s));
   BT_TRY(sc.alloc(&ctx.Hs, n / kPrefixStride + 2));
+  {
+    uint64_t pb[kPrefixStride + 1];
+    pb[0] = 1;
+    for (uint32_t k = 1; k <= kPrefixStride; k++)
+      pb[k] = t->q == Mersenne61::Q ? Mersenne61{}.mul(pb[k - 1], t->B) : SmallMod{t->q}.mul(pb[k - 1], t->B);
+    BT_TRY(sc.alloc(&ctx.PB, kPrefixStride + 1));
+    BT_CUDA(cudaMemcpyAsync(ctx.PB, pb, sizeof(pb), cudaMemcpyHostToDevice, s));
+    BT_CUDA(cudaStreamSynchronize(s));
+  }
   BT_TRY(prefix_fingerprints(dT, n, t->B, t->q, ctx.Hs, s));
   BT_TRY(build_levels(ctx));
   if (t->prune) BT_TRY(prune_tree(ctx, o.max_rounds));

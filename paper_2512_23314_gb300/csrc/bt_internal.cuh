@@ -106,6 +106,48 @@ __device__ __forceinline__ uint64_t window_fp(const M& m, const uint8_t* __restr
   return m.sub(prefix_at(m, T, Hs, B, p + len), m.mul(prefix_at(m, T, Hs, B, p), BL));
 }
 
+// Faster form of prefix_at for q = 2^61-1 with a table PB[k] = B^k, k <= 32:
+//   H(p) = H(32 j) * B^d + sum_{i<d} (T[32 j + i] + 1) * B^(d-1-i),  d = p - 32 j.
+// The sum is accumulated exactly in two 64-bit halves (products of a 9-bit
+// symbol with the low / high 32 bits of B^k) and reduced once.
+__device__ __forceinline__ uint64_t prefix_fast(const Mersenne61& m, const uint8_t* __restrict__ T,
+                                               const uint64_t* __restrict__ Hs,
+                                               const uint64_t* __restrict__ PB, uint64_t p) {
+  const uint64_t j = p / kPrefixStride;
+  const uint32_t d = (uint32_t)(p - j * kPrefixStride);
+  uint64_t h = Hs[j];
+  if (d == 0) return h;
+  const uint8_t* t = T + j * kPrefixStride;
+  uint64_t lo = 0, hi = 0;
+  for (uint32_t i = 0; i < d; i++) {
+    const uint64_t pw = PB[d - 1 - i];
+    const uint64_t c = (uint64_t)t[i] + 1;
+    lo += c * (uint32_t)pw;
+    hi += c * (uint32_t)(pw >> 32);
+  }
+  const uint64_t vlo = lo + (hi << 32);
+  const uint64_t vhi = (hi >> 32) + (vlo < lo ? 1 : 0);
+  uint64_t r = (vlo & Mersenne61::Q) + (vlo >> 61) + (vhi << 3);
+  r = (r & Mersenne61::Q) + (r >> 61);
+  r = r >= Mersenne61::Q ? r - Mersenne61::Q : r;
+  return m.add(m.mul(h, PB[d]), r);
+}
+
+__device__ __forceinline__ uint64_t prefix_fast(const SmallMod& m, const uint8_t* __restrict__ T,
+                                               const uint64_t* __restrict__ Hs,
+                                               const uint64_t* __restrict__ PB, uint64_t p) {
+  (void)PB;
+  return prefix_at(m, T, Hs, PB[1], p);
+}
+
+template <class M>
+__device__ __forceinline__ uint64_t window_fast(const M& m, const uint8_t* __restrict__ T,
+                                               const uint64_t* __restrict__ Hs,
+                                               const uint64_t* __restrict__ PB, uint64_t BL,
+                                               uint64_t p, uint64_t len) {
+  return m.sub(prefix_fast(m, T, Hs, PB, p + len), m.mul(prefix_fast(m, T, Hs, PB, p), BL));
+}
+
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
   x ^= x >> 31;
   x *= 0x7FB5D329728EA185ull;
@@ -275,10 +317,12 @@ struct BuildCtx {
   bt_tree* t;
   const uint8_t* T;   // device text
   uint64_t* Hs;       // prefix fingerprints
+  uint64_t* PB;       // B^k, k = 0..32
   Status* st;         // device status
   Status* st_host;    // pinned mirror
   cudaStream_t s;
   uint64_t verify_bytes = 0, collisions = 0;
+  int dense_scan = 0;  // probe every window (diagnostic) instead of the anchored scan
 };
 
 int build_levels(BuildCtx& ctx);

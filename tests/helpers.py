@@ -18,7 +18,7 @@ def level_blocks(p: "oracle.Parsed"):
         out.append((st, ln))
         if l + 1 < len(p.levels):
             bn = p.levels[l + 1].b
-            m = np.array(lv.marks, dtype=bool)
+            m = np.asarray(lv.marks, dtype=bool)
             ps, pl = st[m], ln[m]
             nch = (pl + bn - 1) // bn
             par = np.repeat(np.arange(len(ps)), nch)
@@ -31,17 +31,17 @@ def level_blocks(p: "oracle.Parsed"):
 def check_pointers(T: np.ndarray, blob: bytes, sample: int | None = None, seed: int = 0):
     """Every (or a sample of) pointer copies its source, lies strictly left,
     targets marked blocks; the leaf text equals the marked last-level blocks."""
-    p = oracle.parse(blob)
+    p = oracle.parse(blob, as_numpy=True)
     rng = np.random.default_rng(seed)
     blocks = level_blocks(p)
     for lv, (st, ln) in zip(p.levels, blocks):
-        marks = np.array(lv.marks, dtype=bool)
+        marks = np.asarray(lv.marks, dtype=bool)
         assert len(marks) == len(st)
         un = np.flatnonzero(~marks)
         assert len(un) == len(lv.ptrs)
         if len(un) == 0:
             continue
-        pa = np.array(lv.ptrs, dtype=np.int64).reshape(-1, 2)
+        pa = np.asarray(lv.ptrs, dtype=np.int64).reshape(-1, 2)
         pick = np.arange(len(un)) if sample is None or sample >= len(un) else \
             rng.choice(len(un), sample, replace=False)
         for i in pick:
@@ -55,7 +55,7 @@ def check_pointers(T: np.ndarray, blob: bytes, sample: int | None = None, seed: 
                 assert st[j + 1] == st[j] + ln[j] and marks[j + 1]
             assert np.array_equal(T[tgt:tgt + L], T[s:s + L])
     st, ln = blocks[-1]
-    m = np.array(p.levels[-1].marks, dtype=bool)
+    m = np.asarray(p.levels[-1].marks, dtype=bool)
     if sample is None:
         leaf = np.concatenate([T[a:a + b] for a, b in zip(st[m], ln[m])]) if m.any() else \
             np.zeros(0, np.uint8)
@@ -69,9 +69,9 @@ def check_leftmost_sampled(T: np.ndarray, p, blocks, per_level: int = 20, seed: 
     Tb = T.tobytes()
     rng = np.random.default_rng(seed)
     for lv, (st, ln) in zip(p.levels, blocks):
-        marks = np.array(lv.marks, dtype=bool)
+        marks = np.asarray(lv.marks, dtype=bool)
         un = np.flatnonzero(~marks)
-        pa = np.array(lv.ptrs, dtype=np.int64).reshape(-1, 2)
+        pa = np.asarray(lv.ptrs, dtype=np.int64).reshape(-1, 2)
         for i in (rng.choice(len(un), min(per_level, len(un)), replace=False) if len(un) else []):
             u = un[i]
             j, off = pa[i]

@@ -207,3 +207,38 @@ def test_config_dna_copies_1mib_full():
     assert blob == ref.export()
     assert t.stats()[0]["b"] == 1 << 19 and len(t.stats()) == 16
     run_queries(t, T, 100_000, 11)
+
+
+def _runs_text(n, seed, alphabet=b"ab", max_run=200):
+    rng = np.random.default_rng(seed)
+    out = bytearray()
+    while len(out) < n:
+        out += bytes([alphabet[rng.integers(len(alphabet))]]) * int(rng.integers(1, max_run))
+    return np.frombuffer(bytes(out[:n]), np.uint8)
+
+
+@pytest.mark.parametrize("dense", [False, True])
+def test_anchored_and_dense_scans(dense):
+    """Both window-scan strategies give the oracle's tree, including texts whose
+    keys have no anchor (long runs) and short tails of every length."""
+    cases = [
+        (_runs_text(50_000, 1), 2, 8), (_runs_text(120_001, 2, b"abc", 500), 4, 16),
+        (_runs_text(30_000, 3, b"a", 2), 2, 4), (np.full(100_003, 65, np.uint8), 4, 32),
+        (workloads.dna_genome(n=600_000 + 37, genome_len=40_000, nrun_rate=1e-3, seed=9), 4, 64),
+        (workloads.text_versions(n=333_333, base_len=20_000, sigma=96, seed=2), 4, 32),
+        (workloads.text_versions(n=99_999, base_len=4096, sigma=4, seed=3), 2, 1),
+        (workloads.random_bytes(70_001, 3, 4), 3, 2),
+    ]
+    for T, tau, leaf in cases:
+        for prune in (True, False):
+            ref = oracle.build(T, tau, leaf, prune=prune).export()
+            _, blob = gpu_export(T, 256, tau, leaf, prune=prune, dense_scan=dense)
+            assert blob == ref, (len(T), tau, leaf, prune)
+    rng = random.Random(7)
+    for _ in range(150):
+        n = rng.randrange(1, 3000)
+        text = _random_text(rng, n, rng.choice([1, 2, 3, 26]))
+        tau, leaf = rng.choice([2, 3, 4]), rng.choice([1, 3, 8, 40, 100])
+        ref = oracle.build(text, tau, leaf).export()
+        _, blob = gpu_export(text, 256, tau, leaf, dense_scan=dense)
+        assert blob == ref, (text, tau, leaf)
