@@ -149,6 +149,33 @@ int bt_stats(const bt_tree* t, uint64_t* out, uint64_t cap);
 int bt_prefix_fingerprints(const uint8_t* d_text, uint64_t n, uint64_t seed, uint64_t modulus,
                            uint32_t stride, uint64_t* d_out, void* stream);
 
+/*
+ * bt_prefix_fingerprints without allocating device memory.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate.
+ * Examples: a host runtime that hands all device memory to its own allocator
+ * up front and forbids libraries it loads to call cudaMalloc, or code on a
+ * latency-critical path that cannot risk an allocation's implicit
+ * synchronisation or its failure.
+ *
+ * Same arguments, results and stream semantics as bt_prefix_fingerprints.
+ * The caller still provides d_text and d_out.  The scratch (power tables and
+ * per-CTA aggregates) is a fixed 528 KiB array in device memory, which every
+ * GPU that loads the library holds until the process exits.  The entry point
+ * calls no cudaMalloc, cudaFree or allocating library routine.
+ *  - n may be at most 2^31 (2 GiB); larger texts return BT_ERANGE before any
+ *    work is queued.
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current) and caches it; make that first call before any
+ *    stream capture.
+ *  - Every call shares the one array: calls whose work overlaps on the GPU
+ *    (for example on two streams) race and give wrong results; serialise
+ *    them.  No scratch entry needs to start at zero: each call writes every
+ *    entry it reads before reading it.
+ */
+int bt_prefix_fingerprints_noalloc(const uint8_t* d_text, uint64_t n, uint64_t seed,
+                                   uint64_t modulus, uint32_t stride, uint64_t* d_out,
+                                   void* stream);
+
 /* The base B selected by seed for modulus (0 = 2^61-1). */
 uint64_t bt_fingerprint_base(uint64_t seed, uint64_t modulus);
 

@@ -65,6 +65,7 @@ def lib() -> ctypes.CDLL:
     L.bt_levels.restype = u32
     L.bt_stats.argtypes = [vp, P(u64), u64]
     L.bt_prefix_fingerprints.argtypes = [vp, u64, u64, u64, u32, vp, vp]
+    L.bt_prefix_fingerprints_noalloc.argtypes = [vp, u64, u64, u64, u32, vp, vp]
     L.bt_fingerprint_base.argtypes = [u64, u64]
     L.bt_fingerprint_base.restype = u64
     L.bt_free.argtypes = [vp]
@@ -79,7 +80,8 @@ def lib() -> ctypes.CDLL:
     L.bt_launch_count.argtypes = []
     L.bt_launch_count.restype = u64
     for name in ("bt_profile_read", "bt_build", "bt_build_ex", "bt_access", "bt_rank", "bt_select",
-                 "bt_query_batch", "bt_export", "bt_stats", "bt_prefix_fingerprints"):
+                 "bt_query_batch", "bt_export", "bt_stats", "bt_prefix_fingerprints",
+                 "bt_prefix_fingerprints_noalloc"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -194,6 +196,13 @@ def bt_prefix_fingerprints(d_text, n: int, seed: int, modulus: int, stride: int,
     _check(lib().bt_prefix_fingerprints(d_text.data_ptr(), n, seed, modulus, stride,
                                         d_out.data_ptr(), _stream_ptr(stream)),
            "bt_prefix_fingerprints")
+
+
+def bt_prefix_fingerprints_noalloc(d_text, n: int, seed: int, modulus: int, stride: int, d_out,
+                                   stream=None) -> None:
+    _check(lib().bt_prefix_fingerprints_noalloc(d_text.data_ptr(), n, seed, modulus, stride,
+                                                d_out.data_ptr(), _stream_ptr(stream)),
+           "bt_prefix_fingerprints_noalloc")
 
 
 def bt_fingerprint_base(seed: int, modulus: int = 0) -> int:

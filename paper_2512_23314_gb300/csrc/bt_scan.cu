@@ -13,6 +13,7 @@
 // Three passes: a CTA-local scan of 1024 items, a single-CTA scan of the CTA
 // aggregates, and a pass that folds each CTA's prefix into its items.
 #include <cstdio>
+#include <mutex>
 
 #include "bt_internal.cuh"
 
@@ -236,5 +237,103 @@ int prefix_fingerprints(const uint8_t* T, uint64_t n, uint64_t B, uint64_t q, ui
   if (q == Mersenne61::Q) return kr_prefix(Mersenne61{}, T, n, B, Hs, s);
   return kr_prefix(SmallMod{q}, T, n, B, Hs, s);
 }
+
+// ---------------------------------------------------------------------------
+// Prefix fingerprints without allocation (bt_prefix_fingerprints_noalloc).
+//
+// Some callers cannot allocate device memory.  For example, a host runtime may
+// reserve all device memory for its own allocator up front and forbid the
+// libraries it loads to call cudaMalloc.  Code on a latency-critical path may
+// also be unable to risk an allocation's implicit synchronisation or failure.
+// This variant of the prefix-fingerprint pass takes its scratch (the two power
+// tables and the per-CTA aggregates) from a fixed array in device memory
+// instead of cudaMallocAsync.  Every GPU that loads the library holds the
+// array until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr uint64_t kNoAllocMaxN = 1ull << 31;  // largest text accepted (2 GiB)
+constexpr uint64_t kNoAllocAggs = (kNoAllocMaxN / kPrefixStride + kTile - 1) / kTile;
+constexpr uint64_t kNoAllocWords = 2 * (kTile + 1) + kNoAllocAggs;  // 67586 u64, 528 KiB
+constexpr int kNoAllocDevices = 64;
+
+static __device__ __align__(256) uint64_t g_noalloc_scratch[kNoAllocWords];
+
+std::mutex g_noalloc_mu;
+uint64_t* g_noalloc_addr[kNoAllocDevices] = {};
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name stands for a host-side shadow, not device memory, so the
+// address is looked up once per device (the first call on a device does it)
+// and cached.
+int noalloc_scratch(uint64_t** out) {
+  int dev = 0;
+  BT_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocDevices) return BT_EINVAL;
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+      note_cuda_error(e, "cudaGetSymbolAddress", __FILE__, __LINE__);
+      return BT_ECUDA;
+    }
+    g_noalloc_addr[dev] = (uint64_t*)p;
+  }
+  *out = g_noalloc_addr[dev];
+  return BT_OK;
+}
+
+// pw1[i] = P^i and pw2[i] = P^(1024 i) for i <= 1024, P = B^32, computed on
+// the device so that no host buffer has to be copied.
+template <class M>
+__global__ void k_kr_powers(M m, uint64_t B, uint64_t* __restrict__ pw) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i > (uint64_t)kTile) return;
+  const uint64_t P = pow_mod(m, B, kPrefixStride);
+  pw[i] = pow_mod(m, P, i);
+  pw[kTile + 1 + i] = pow_mod(m, pow_mod(m, P, kTile), i);
+}
+
+template <class M>
+int kr_prefix_noalloc(const M& m, const uint8_t* T, uint64_t n, uint64_t B, uint64_t* Hs,
+                      uint64_t* scratch, cudaStream_t s) {
+  const uint64_t nchunks = n / kPrefixStride;
+  if (nchunks == 0) {
+    BT_CUDA(cudaMemsetAsync(Hs, 0, sizeof(uint64_t), s));
+    return BT_OK;
+  }
+  const uint64_t na = (nchunks + kTile - 1) / kTile;
+  uint64_t* pw = scratch;
+  uint64_t* agg = scratch + 2 * (kTile + 1);
+  BT_LAUNCH(k_kr_powers<M><<<(kTile + 1 + 255) / 256, 256, 0, s>>>(m, B, pw));
+  BT_LAUNCH(k_kr_local<M><<<(unsigned)na, kTile, 0, s>>>(m, T, nchunks, B, pw, Hs, agg));
+  BT_LAUNCH(k_kr_aggs<M><<<1, kTile, 0, s>>>(m, agg, na, pw + kTile + 1));
+  BT_LAUNCH(k_kr_add<M><<<(unsigned)na, kTile, 0, s>>>(m, Hs, nchunks, agg, pw));
+  BT_CUDA(cudaGetLastError());
+  return BT_OK;
+}
+
+}  // namespace
+
+}  // namespace bt
+
+extern "C" int bt_prefix_fingerprints_noalloc(const uint8_t* d_text, uint64_t n, uint64_t seed,
+                                              uint64_t modulus, uint32_t stride, uint64_t* d_out,
+                                              void* stream) {
+  using namespace bt;
+  if (!d_text || !d_out || stride != kPrefixStride) return BT_EINVAL;
+  if (modulus && (modulus < 300 || modulus >= (1ull << 32))) return BT_EINVAL;
+  if (n > kNoAllocMaxN) return BT_ERANGE;
+  uint64_t* scratch = nullptr;
+  BT_TRY(noalloc_scratch(&scratch));
+  const uint64_t q = modulus ? modulus : Mersenne61::Q;
+  const uint64_t B = bt_fingerprint_base(seed, modulus);
+  cudaStream_t s = stream ? (cudaStream_t)stream : cudaStreamPerThread;
+  if (q == Mersenne61::Q) return kr_prefix_noalloc(Mersenne61{}, d_text, n, B, d_out, scratch, s);
+  return kr_prefix_noalloc(SmallMod{q}, d_text, n, B, d_out, scratch, s);
+}
+
+namespace bt {
 
 }  // namespace bt
