@@ -103,21 +103,19 @@ static int plan_sizes(uint64_t n, uint32_t tau, uint32_t leaf, const bt_opts& o,
   return BT_OK;
 }
 
+// Tree arrays come from the stream-ordered pool (cudaMallocAsync); they are
+// returned the same way and the stream is synchronised once.
 static void free_tree_memory(bt_tree* t) {
+  cudaStream_t s = cudaStreamPerThread;
   for (Level& v : t->lv) {
-    cudaFree(v.st);
-    cudaFree(v.mw);
-    cudaFree(v.mr);
-    cudaFree(v.ptr);
-    cudaFree(v.off);
-    cudaFree(v.lo);
-    cudaFree(v.cnt);
-    cudaFree(v.pc);
+    void* arrays[] = {v.st, v.mw, v.mr, v.ptr, v.off, v.lo, v.cnt, v.pc};
+    for (void* a : arrays)
+      if (a) cudaFreeAsync(a, s);
   }
-  cudaFree(t->leaf);
-  cudaFree(t->pre);
-  cudaFree(t->sym);
-  cudaFree(t->view);
+  void* rest[] = {t->leaf, t->pre, t->sym, t->view};
+  for (void* a : rest)
+    if (a) cudaFreeAsync(a, s);
+  cudaStreamSynchronize(s);
 }
 
 static int build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, uint32_t leaf,
@@ -161,7 +159,10 @@ static int build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, 
     ~HostFree() { cudaFreeHost(p); }
   } hf{ctx.st_host};
 
-  BT_TRY(alphabet(dT, n, sigma, t, s));
+  {
+    ProfScope ps("phase_alphabet", s, n);
+    BT_TRY(alphabet(dT, n, sigma, t, s));
+  }
   BT_TRY(sc.alloc(&ctx.Hs, n / kPrefixStride + 2));
   {
     uint64_t pb[kPrefixStride + 1];
@@ -173,11 +174,20 @@ static int build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, 
     BT_CUDA(cudaStreamSynchronize(s));
   }
   BT_TRY(prefix_fingerprints(dT, n, t->B, t->q, ctx.Hs, s));
-  BT_TRY(build_levels(ctx));
-  if (t->prune) BT_TRY(prune_tree(ctx, o.max_rounds));
-  else
-    for (Level& v : t->lv) v.stats[BT_ST_FINAL_BLOCKS] = v.c;
-  BT_TRY(build_counters(ctx));
+  {
+    ProfScope ps("phase_levels", s, 0);
+    BT_TRY(build_levels(ctx));
+  }
+  {
+    ProfScope ps("phase_prune", s, 0);
+    if (t->prune) BT_TRY(prune_tree(ctx, o.max_rounds));
+    else
+      for (Level& v : t->lv) v.stats[BT_ST_FINAL_BLOCKS] = v.c;
+  }
+  {
+    ProfScope ps("phase_counters", s, 0);
+    BT_TRY(build_counters(ctx));
+  }
   for (Level& v : t->lv) {
     cudaFreeAsync(v.lo, s);
     v.lo = nullptr;

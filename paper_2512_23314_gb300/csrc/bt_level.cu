@@ -288,6 +288,7 @@ struct AnchorSet {
   uint32_t gram;             // remapped gram hash (kEmptyGram: empty slot)
   uint32_t pad;
   unsigned long long offs;   // bit a: some key has its anchor at offset a
+  unsigned long long maxst;  // largest start of a key anchored on this gram
 };
 
 __device__ __forceinline__ uint32_t gram_hash(const uint8_t* __restrict__ T, uint64_t x, uint32_t w,
@@ -316,8 +317,10 @@ __device__ __forceinline__ uint32_t sec_bit(uint32_t g) { return (g * 0x2545F491
 
 __global__ void k_clear_offs(AnchorSet* atab, uint64_t cap) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < cap;
-       i += (uint64_t)gridDim.x * blockDim.x)
+       i += (uint64_t)gridDim.x * blockDim.x) {
     atab[i].offs = 0;
+    atab[i].maxst = 0;
+  }
 }
 
 // Register the anchor of every key (every block and the tail).
@@ -369,6 +372,7 @@ __global__ void k_anchor_keys(Geo g, GramP gp, const uint32_t* __restrict__ slot
       const uint32_t cur = atomicCAS(&atab[h].gram, kEmptyGram, gk);
       if (cur == kEmptyGram || cur == gk) {
         atomicOr(&atab[h].offs, 1ull << a);
+        atomicMax(&atab[h].maxst, (unsigned long long)s);
         placed = true;
       } else {
         h = (h + 1) & amask;
@@ -514,7 +518,7 @@ __device__ __forceinline__ void stage(uint8_t* slot, const uint8_t* __restrict__
 }
 
 template <class M>
-__global__ void __launch_bounds__(kScanThreads) k_scan_anchor(ScanCtx<M> C0, GramP gp, uint64_t cpb,
+__global__ void __launch_bounds__(kScanThreads, 3) k_scan_anchor(ScanCtx<M> C0, GramP gp, uint64_t cpb,
                                                              const AnchorSet* __restrict__ atab,
                                                              uint32_t amask,
                                                              const uint32_t* __restrict__ bitmap_g,
@@ -605,19 +609,23 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_anchor(ScanCtx<M> C0, Gra
         if (!is_anchor) continue;
         const uint32_t gk = gram_key(gx);
         if (gk == tail_gram && x >= tail_a) propose(C, k, s, av, x - tail_a, 1, ncand, nhit);
-        unsigned long long offs = 0;
+        unsigned long long offs = 0, maxst = 0;
         for (uint32_t h = gram_slot(gk, amask), it = 0; it <= amask; h = (h + 1) & amask, it++) {
           const uint32_t eg = atab[h].gram;
           if (eg == gk) {
             offs = atab[h].offs;
+            maxst = atab[h].maxst;
             break;
           }
           if (eg == kEmptyGram) break;
         }
+        // A window that starts after every key anchored on this gram cannot
+        // be the leftmost occurrence of any of them, nor of a pair that
+        // starts with one of them (both are at or before the key's start).
         while (offs) {
           const uint32_t a = __ffsll(offs) - 1;
           offs &= offs - 1;
-          if (a <= x) propose(C, k, s, av, x - a, 0, ncand, nhit);
+          if (a <= x && x - a <= maxst) propose(C, k, s, av, x - a, 0, ncand, nhit);
         }
       }
     }

@@ -292,7 +292,7 @@ int alphabet(const uint8_t* T, uint64_t n, uint32_t sigma, bt_tree* t, cudaStrea
   for (int i = 0; i < 256; i++) t->sym_host[i] = h[i] ? (int16_t)S++ : (int16_t)-1;
   if (S > sigma) return BT_EINVAL;
   t->S = S;
-  BT_CUDA(cudaMalloc(&t->sym, 256 * sizeof(int16_t)));
+  BT_CUDA(cudaMallocAsync(&t->sym, 256 * sizeof(int16_t), s));
   BT_CUDA(cudaMemcpyAsync(t->sym, t->sym_host, 256 * sizeof(int16_t), cudaMemcpyHostToDevice, s));
   BT_CUDA(cudaStreamSynchronize(s));
   return BT_OK;
@@ -363,7 +363,7 @@ int upload_view(bt_tree* t, cudaStream_t s) {
   h.pre = t->pre;
   h.leaf = t->leaf;
   h.sym = t->sym;
-  BT_CUDA(cudaMalloc(&t->view, sizeof(TreeView)));
+  BT_CUDA(cudaMallocAsync(&t->view, sizeof(TreeView), s));
   BT_CUDA(cudaMemcpyAsync(t->view, &h, sizeof(TreeView), cudaMemcpyHostToDevice, s));
   BT_CUDA(cudaStreamSynchronize(s));
   return BT_OK;
