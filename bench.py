@@ -70,6 +70,8 @@ def parse_args():
     ap.add_argument("--cpu-sample-mib", type=int, default=8,
                     help="prefix of the workload the CPU oracle builds per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-build and serving measurements")
     return ap.parse_args()
 
 
@@ -190,6 +192,59 @@ def cpu_baseline(text: np.ndarray, w: dict, sample_mib: int, steps: int = 1) -> 
     return {"value": n / sec / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {n} bytes ({n >> 20} MiB) of the workload text, prune on, "
                       f"median of {steps} single-threaded builds"}
+
+
+def measure_batch(ndocs: int = 512, min_len: int = 4 << 10, max_len: int = 1 << 20,
+                  nworkers: int = 16) -> dict:
+    """Many small documents (the batched workload scaled down): one document
+    per bt_build_ex call, back to back, against one bt_build_batch call.
+    Texts start in host memory in both arms; trees are freed after timing."""
+    import torch
+
+    from paper_2512_23314_gb300 import bt
+    docs = workloads.doc_mix(ndocs, min_len=min_len, max_len=max_len, seed=0xB7EE0004)
+    args = ([d.text for d in docs], [len(d.text) for d in docs], [d.sigma for d in docs],
+            [d.tau for d in docs], [d.leaf_len for d in docs])
+    warm = bt.bt_build_batch(*(a[:16] for a in args), nworkers=nworkers)
+    for h in warm:
+        bt.bt_free(h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hs = []
+    for d in docs:
+        hs.append(bt.bt_build_ex(d.text, len(d.text), d.sigma, d.tau, d.leaf_len))
+    plain_s = time.perf_counter() - t0
+    for h in hs:
+        bt.bt_free(h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hs = bt.bt_build_batch(*args, nworkers=nworkers)
+    batch_s = time.perf_counter() - t0
+    for h in hs:
+        bt.bt_free(h)
+    total = sum(len(d.text) for d in docs)
+    return {"workload": f"{ndocs} versioned-text documents, log-uniform {min_len >> 10} KiB - "
+                        f"{max_len >> 20} MiB, sigma 4-128, tau 2/4/8, leaf 32",
+            "docs": ndocs, "bytes": total, "nworkers": nworkers,
+            "docs_per_s": ndocs / batch_s, "plain_docs_per_s": ndocs / plain_s,
+            "speedup": plain_s / batch_s, "batch_mb_per_s": total / batch_s / 1e6,
+            "plain_mb_per_s": total / plain_s / 1e6}
+
+
+def measure_serve(rate: float = 2000.0, duration: float = 0.25, min_len: int = 1 << 10,
+                  max_len: int = 2 << 20, nworkers: int = 16) -> dict:
+    """The serving loop on a scaled-down arrival stream."""
+    from paper_2512_23314_gb300 import serve
+    arrivals = workloads.serve_arrivals(rate=rate, duration=duration, min_len=min_len,
+                                        max_len=max_len)
+    srv = serve.Server(hbm_budget=120 << 30, nworkers=nworkers, queries_per_doc=10_000)
+    rep = srv.run(arrivals)
+    srv.close()
+    out = rep.summary()
+    out["workload"] = (f"Poisson {rate:.0f} docs/s for {duration} s, log-uniform "
+                       f"{min_len >> 10} KiB - {max_len >> 20} MiB, DNA-like / text-like 50/50, "
+                       f"120 GiB budget, {out['queries_per_doc']} queries per document")
+    return out
 
 
 def run_reference(args):
@@ -342,6 +397,9 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if world == 1 and not args.no_extras:
+        line["batch"] = measure_batch()
+        line["serve"] = measure_serve()
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(text, w, args.cpu_sample_mib)
     print(json.dumps(line), flush=True)

@@ -91,6 +91,22 @@ int bt_build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau,
 int bt_build_ex(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau,
                 uint32_t leaf_len, const bt_opts* opts, void* stream, bt_tree** out);
 
+/*
+ * Build the trees of ndocs independent texts in one call.  Document d is
+ * texts[d][0, ns[d]) with sigmas[d], taus[d], leaf_lens[d]; every document
+ * uses *opts (NULL: defaults).  Texts may be host or device pointers.  The
+ * documents are distributed over `nworkers` host workers (0: 8), each issuing
+ * its builds on its own CUDA stream, so the small kernels and per-level
+ * synchronisations of different documents overlap on the GPU.  Each tree is
+ * identical to the one bt_build_ex makes for that document alone.  On success
+ * outs[d] holds document d's tree; if any build fails, every tree of the
+ * batch is freed, outs[] is set to NULL and the first failure's status is
+ * returned.
+ */
+int bt_build_batch(const uint8_t* const* texts, const uint64_t* ns, const uint32_t* sigmas,
+                   const uint32_t* taus, const uint32_t* leaf_lens, uint64_t ndocs,
+                   const bt_opts* opts, uint32_t nworkers, bt_tree** outs);
+
 /* access(i) = T[i], 0 <= i < n (section 1).  BT_ERANGE if i >= n. */
 int bt_access(const bt_tree* t, uint64_t i, uint8_t* out);
 
@@ -124,6 +140,9 @@ int bt_query_batch(const bt_tree* t, int kind, const uint64_t* d_args, uint64_t 
  * small buffer returns BT_ERANGE.
  */
 int bt_export(const bt_tree* t, uint8_t* buf, uint64_t cap, uint64_t* len);
+
+/* Device memory held by a built tree, in bytes (levels, counters, leaf text). */
+uint64_t bt_device_bytes(const bt_tree* t);
 
 /* Number of levels of a built tree. */
 uint32_t bt_levels(const bt_tree* t);

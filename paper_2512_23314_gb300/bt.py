@@ -56,11 +56,14 @@ def lib() -> ctypes.CDLL:
     L.bt_opts_default.restype = None
     L.bt_build.argtypes = [vp, u64, u32, u32, u32, P(vp)]
     L.bt_build_ex.argtypes = [vp, u64, u32, u32, u32, P(bt_opts), vp, P(vp)]
+    L.bt_build_batch.argtypes = [vp, vp, vp, vp, vp, u64, P(bt_opts), u32, vp]
     L.bt_access.argtypes = [vp, u64, P(u8)]
     L.bt_rank.argtypes = [vp, u8, u64, P(u64)]
     L.bt_select.argtypes = [vp, u8, u64, P(u64)]
     L.bt_query_batch.argtypes = [vp, ctypes.c_int, vp, u64, vp, vp]
     L.bt_export.argtypes = [vp, vp, u64, P(u64)]
+    L.bt_device_bytes.argtypes = [vp]
+    L.bt_device_bytes.restype = u64
     L.bt_levels.argtypes = [vp]
     L.bt_levels.restype = u32
     L.bt_stats.argtypes = [vp, P(u64), u64]
@@ -79,7 +82,7 @@ def lib() -> ctypes.CDLL:
     L.bt_profile_read.argtypes = [vp, u32, P(u32)]
     L.bt_launch_count.argtypes = []
     L.bt_launch_count.restype = u64
-    for name in ("bt_profile_read", "bt_build", "bt_build_ex", "bt_access", "bt_rank", "bt_select",
+    for name in ("bt_profile_read", "bt_build", "bt_build_ex", "bt_build_batch", "bt_access", "bt_rank", "bt_select",
                  "bt_query_batch", "bt_export", "bt_stats", "bt_prefix_fingerprints",
                  "bt_prefix_fingerprints_noalloc"):
         getattr(L, name).restype = ctypes.c_int
@@ -149,6 +152,25 @@ def bt_build_ex(text, n: int, sigma: int, tau: int, leaf_len: int, opts: bt_opts
     return h.value
 
 
+def bt_build_batch(texts, ns, sigmas, taus, leaf_lens, opts: bt_opts | None = None,
+                   nworkers: int = 0) -> list[int]:
+    """Build many documents in one call; returns one tree handle per document."""
+    nd = len(texts)
+    keep = [_text_ptr(t) for t in texts]
+    ptrs = (ctypes.c_void_p * max(1, nd))(*[k[0] for k in keep])
+    a_ns = np.ascontiguousarray(ns, dtype=np.uint64)
+    a_sg = np.ascontiguousarray(sigmas, dtype=np.uint32)
+    a_tau = np.ascontiguousarray(taus, dtype=np.uint32)
+    a_leaf = np.ascontiguousarray(leaf_lens, dtype=np.uint32)
+    outs = (ctypes.c_void_p * max(1, nd))()
+    o = opts if opts is not None else bt_opts_default()
+    _check(lib().bt_build_batch(ptrs, a_ns.ctypes.data, a_sg.ctypes.data, a_tau.ctypes.data,
+                                a_leaf.ctypes.data, nd, ctypes.byref(o), nworkers, outs),
+           "bt_build_batch")
+    del keep
+    return [outs[i] for i in range(nd)]
+
+
 def bt_access(t: int, i: int) -> int:
     out = ctypes.c_uint8()
     _check(lib().bt_access(t, i, ctypes.byref(out)), "bt_access")
@@ -178,6 +200,10 @@ def bt_export(t: int) -> bytes:
     buf = (ctypes.c_uint8 * n.value)()
     _check(lib().bt_export(t, buf, n.value, ctypes.byref(n)), "bt_export")
     return bytes(buf)
+
+
+def bt_device_bytes(t: int) -> int:
+    return int(lib().bt_device_bytes(t))
 
 
 def bt_levels(t: int) -> int:

@@ -11,6 +11,7 @@
 #include <atomic>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "bt_internal.cuh"
@@ -193,6 +194,12 @@ static int build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, 
     v.lo = nullptr;
   }
   BT_TRY(upload_view(t, s));
+  uint64_t bytes = t->leaf_bytes + 16 + sizeof(TreeView) + 512 + (t->lv[0].c + 1) * t->S * 8;
+  for (const Level& v : t->lv) {
+    const uint64_t words = (v.c + 31) / 32;
+    bytes += v.c * (8 + 4 + 8) + (2 * words + 1) * 4 + 2 * v.c * t->S * 4;
+  }
+  t->dev_bytes = bytes;
   BT_CUDA(cudaStreamSynchronize(s));
   BT_TRY(sync_status(ctx));
   if (ctx.st_host->error) return BT_EINTERNAL;
@@ -244,6 +251,54 @@ int bt_build_ex(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, u
 int bt_build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, uint32_t leaf_len,
              bt_tree** out) {
   return bt_build_ex(text, n, sigma, tau, leaf_len, nullptr, nullptr, out);
+}
+
+int bt_build_batch(const uint8_t* const* texts, const uint64_t* ns, const uint32_t* sigmas,
+                   const uint32_t* taus, const uint32_t* leaf_lens, uint64_t ndocs,
+                   const bt_opts* opts, uint32_t nworkers, bt_tree** outs) {
+  if (!outs || (ndocs && (!texts || !ns || !sigmas || !taus || !leaf_lens))) return BT_EINVAL;
+  for (uint64_t d = 0; d < ndocs; d++) outs[d] = nullptr;
+  if (ndocs == 0) return BT_OK;
+  if (nworkers == 0) nworkers = 8;
+  if (nworkers > ndocs) nworkers = (uint32_t)ndocs;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) {
+    cudaGetLastError();
+    return BT_ECUDA;
+  }
+  std::atomic<uint64_t> next{0};
+  std::atomic<int> first_error{BT_OK};
+  auto worker = [&]() {
+    cudaSetDevice(device);
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      int expect = BT_OK;
+      first_error.compare_exchange_strong(expect, BT_ECUDA);
+      return;
+    }
+    for (;;) {
+      const uint64_t d = next.fetch_add(1);
+      if (d >= ndocs || first_error.load() != BT_OK) break;
+      const int rc = bt_build_ex(texts[d], ns[d], sigmas[d], taus[d], leaf_lens[d], opts, s, &outs[d]);
+      if (rc != BT_OK) {
+        int expect = BT_OK;
+        first_error.compare_exchange_strong(expect, rc);
+      }
+    }
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  };
+  std::vector<std::thread> pool;
+  for (uint32_t i = 0; i < nworkers; i++) pool.emplace_back(worker);
+  for (auto& th : pool) th.join();
+  const int rc = first_error.load();
+  if (rc != BT_OK) {
+    for (uint64_t d = 0; d < ndocs; d++) {
+      bt_free(outs[d]);
+      outs[d] = nullptr;
+    }
+  }
+  return rc;
 }
 
 void bt_free(bt_tree* t) {
@@ -310,6 +365,8 @@ int bt_query_batch(const bt_tree* t, int kind, const uint64_t* d_args, uint64_t 
 }
 
 uint32_t bt_levels(const bt_tree* t) { return t ? t->L : 0; }
+
+uint64_t bt_device_bytes(const bt_tree* t) { return t ? t->dev_bytes : 0; }
 
 int bt_stats(const bt_tree* t, uint64_t* out, uint64_t cap) {
   if (!t || !out || cap < (uint64_t)t->L * BT_ST_FIELDS) return BT_EINVAL;

@@ -216,6 +216,7 @@ struct bt_tree {
   uint32_t S = 0;
   bt::TreeView* view = nullptr;  // device copy of the view
   int device = 0;
+  uint64_t dev_bytes = 0;        // device memory held by the tree
 };
 
 namespace bt {

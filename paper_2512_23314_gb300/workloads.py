@@ -190,3 +190,36 @@ def doc_mix(ndocs: int, min_len: int = 4 << 10, max_len: int = 16 << 20,
                           seed=int(rng.integers(0, 2**62)))
         docs.append(Doc(t, sigma, tau, leaf_len))
     return docs
+
+
+@dataclass
+class Arrival:
+    t: float          # arrival time in seconds from the start
+    doc: Doc
+
+
+def serve_arrivals(rate: float = 2000.0, duration: float = 10.0, min_len: int = 1 << 10,
+                   max_len: int = 64 << 20, seed: int = 0xB7EE0005) -> list[Arrival]:
+    """Poisson arrivals (exponential gaps at `rate` per second) over
+    `duration` seconds.  Each document has a log-uniform length in
+    [min_len, max_len] and is, with equal probability, DNA-like (a random
+    genome of len/16 bases copied with SNPs, indels and N runs; tau 4,
+    leaf 64) or text-like (a Zipf text of len/16 bytes in versions; tau 4,
+    leaf 32)."""
+    rng = _rng(seed)
+    out = []
+    t = 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            break
+        u = rng.random()
+        length = int(np.floor(np.exp(u * np.log(max_len / min_len)) * min_len))
+        s = int(rng.integers(0, 2**62))
+        if rng.random() < 0.5:
+            text = dna_genome(n=length, genome_len=max(1024, length // 16), seed=s)
+            out.append(Arrival(t, Doc(text, 5, 4, 64)))
+        else:
+            text = text_versions(n=length, base_len=max(1024, length // 16), sigma=96, seed=s)
+            out.append(Arrival(t, Doc(text, 96, 4, 32)))
+    return out

@@ -1,0 +1,62 @@
+"""Batched and served builds give the same trees as standalone builds.
+
+Many small documents built in one bt_build_batch call, and documents built
+by the serving loop while others are on the GPU, must each produce exactly
+the tree that a standalone bt_build_ex makes (and that the oracle makes).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2512_23314_gb300 import bt, serve, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def alone(doc):
+    t = bt.Tree(doc.text, doc.sigma, doc.tau, doc.leaf_len)
+    blob = t.export()
+    t.close()
+    return blob
+
+
+def test_batch_equals_standalone_and_oracle():
+    docs = workloads.doc_mix(40, min_len=1 << 10, max_len=300 << 10, leaf_len=16, seed=77)
+    handles = bt.bt_build_batch([d.text for d in docs], [len(d.text) for d in docs],
+                                [d.sigma for d in docs], [d.tau for d in docs],
+                                [d.leaf_len for d in docs], nworkers=8)
+    try:
+        for d, h in zip(docs, handles):
+            blob = bt.bt_export(h)
+            assert blob == alone(d)
+            if len(d.text) <= 64 << 10:
+                assert blob == oracle.build(d.text, d.tau, d.leaf_len, prune=True).export()
+    finally:
+        for h in handles:
+            bt.bt_free(h)
+
+
+def test_batch_reports_failures_and_frees():
+    docs = workloads.doc_mix(6, min_len=1 << 10, max_len=8 << 10, seed=3)
+    sig = [d.sigma for d in docs]
+    sig[3] = 1  # more distinct bytes than the alphabet size: BT_EINVAL
+    with pytest.raises(bt.BTError) as e:
+        bt.bt_build_batch([d.text for d in docs], [len(d.text) for d in docs], sig,
+                          [d.tau for d in docs], [d.leaf_len for d in docs], nworkers=3)
+    assert e.value.code == bt.BT_EINVAL
+
+
+def test_served_results_equal_standalone():
+    arrivals = workloads.serve_arrivals(rate=2000.0, duration=0.03, min_len=1 << 10,
+                                        max_len=256 << 10, seed=5)
+    assert len(arrivals) > 20
+    srv = serve.Server(hbm_budget=256 << 20, nworkers=6, queries_per_doc=300, keep_exports=True)
+    rep = srv.run(arrivals)
+    srv.close()
+    assert rep.docs == len(arrivals)
+    assert rep.max_concurrent >= 2          # work really overlapped
+    for a, r in zip(arrivals, rep.results):
+        assert r.export == alone(a.doc)
+        assert r.built >= r.arrival and r.queried >= r.built
+    torch.cuda.synchronize()
