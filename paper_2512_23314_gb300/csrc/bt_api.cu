@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <atomic>
+#include <chrono>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -109,9 +110,9 @@ static int plan_sizes(uint64_t n, uint32_t tau, uint32_t leaf, const bt_opts& o,
 static void free_tree_memory(bt_tree* t) {
   cudaStream_t s = cudaStreamPerThread;
   for (Level& v : t->lv) {
-    void* arrays[] = {v.st, v.mw, v.mr, v.ptr, v.off, v.lo, v.cnt, v.pc};
-    for (void* a : arrays)
+    for (void* a : v.owned)
       if (a) cudaFreeAsync(a, s);
+    v.owned.clear();
   }
   void* rest[] = {t->leaf, t->pre, t->sym, t->view};
   for (void* a : rest)
@@ -119,8 +120,40 @@ static void free_tree_memory(bt_tree* t) {
   cudaStreamSynchronize(s);
 }
 
+// Builds allocate and free their scratch through the device's stream-ordered
+// pool.  By default the pool hands unused memory back to the driver at every
+// synchronisation, so each level would map its scratch again; keep it cached
+// for the life of the process instead (this changes only this process's pool).
+static void keep_pool_memory(int device) {
+  static std::mutex mu;
+  static bool done[64] = {};
+  if (device < 0 || device >= 64) return;
+  std::lock_guard<std::mutex> g(mu);
+  if (done[device]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+  done[device] = true;
+}
+
+struct HostTrace {
+  bool on = getenv("BT_TRACE") != nullptr;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  void mark(const char* what) {
+    if (!on) return;
+    auto t1 = std::chrono::steady_clock::now();
+    fprintf(stderr, "bt-trace %s host %.3f ms\n", what,
+            std::chrono::duration<double, std::milli>(t1 - t0).count());
+    t0 = t1;
+  }
+};
+
 static int build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, uint32_t leaf,
                  const bt_opts& o, cudaStream_t s, bt_tree* t) {
+  HostTrace tr;
   std::vector<uint64_t> sizes;
   BT_TRY(plan_sizes(n, tau, leaf, o, sizes));
   t->n = n;
@@ -135,6 +168,7 @@ static int build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, 
   for (uint32_t l = 0; l < t->L; l++) t->lv[l].b = sizes[l];
 
   BT_CUDA(cudaGetDevice(&t->device));
+  keep_pool_memory(t->device);
   Scratch sc(s);
   // Text on the device.
   cudaPointerAttributes pa;
@@ -151,6 +185,7 @@ static int build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, 
   ctx.t = t;
   ctx.T = dT;
   ctx.s = s;
+  ctx.arena.s = s;
   ctx.dense_scan = (o.flags & BT_FLAG_DENSE_SCAN) ? 1 : 0;
   BT_TRY(sc.alloc(&ctx.st, 1));
   BT_CUDA(cudaMemsetAsync(ctx.st, 0, sizeof(Status), s));
@@ -164,6 +199,7 @@ static int build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, 
     ProfScope ps("phase_alphabet", s, n);
     BT_TRY(alphabet(dT, n, sigma, t, s));
   }
+  tr.mark("setup+alphabet");
   BT_TRY(sc.alloc(&ctx.Hs, n / kPrefixStride + 2));
   {
     uint64_t pb[kPrefixStride + 1];
@@ -179,20 +215,21 @@ static int build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, 
     ProfScope ps("phase_levels", s, 0);
     BT_TRY(build_levels(ctx));
   }
+  tr.mark("levels");
   {
     ProfScope ps("phase_prune", s, 0);
     if (t->prune) BT_TRY(prune_tree(ctx, o.max_rounds));
     else
       for (Level& v : t->lv) v.stats[BT_ST_FINAL_BLOCKS] = v.c;
   }
+  tr.mark("prune");
   {
     ProfScope ps("phase_counters", s, 0);
     BT_TRY(build_counters(ctx));
   }
-  for (Level& v : t->lv) {
-    cudaFreeAsync(v.lo, s);
-    v.lo = nullptr;
-  }
+  tr.mark("counters");
+  for (Level& v : t->lv) v.lo = nullptr;  // lives in the level's allocation; no longer needed
+  ctx.arena.release();
   BT_TRY(upload_view(t, s));
   uint64_t bytes = t->leaf_bytes + 16 + sizeof(TreeView) + 512 + (t->lv[0].c + 1) * t->S * 8;
   for (const Level& v : t->lv) {
@@ -202,11 +239,14 @@ static int build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, 
   t->dev_bytes = bytes;
   BT_CUDA(cudaStreamSynchronize(s));
   BT_TRY(sync_status(ctx));
+  tr.mark("finish");
   if (ctx.st_host->error) return BT_EINTERNAL;
   return BT_OK;
 }
 
 static cudaStream_t as_stream(void* s) { return s ? (cudaStream_t)s : cudaStreamPerThread; }
+
+
 
 }  // namespace bt
 

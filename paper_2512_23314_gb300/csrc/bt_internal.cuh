@@ -174,6 +174,7 @@ struct Level {
   uint32_t* cnt = nullptr;
   uint32_t* pc = nullptr;
   uint64_t stats[BT_ST_FIELDS] = {};
+  std::vector<void*> owned;  // device allocations holding this level's arrays
 };
 
 // Device-side view of one level, passed by value to kernels.
@@ -299,6 +300,50 @@ struct Scratch {
   }
 };
 
+// Growable scratch arena of one build: a level carves all its temporary
+// buffers out of one device allocation (a bump pointer reset per level), so
+// a level costs one allocation at most instead of dozens.  In dry mode take()
+// only adds up the bytes a carving needs.
+struct Arena {
+  cudaStream_t s = nullptr;
+  char* base = nullptr;
+  uint64_t cap = 0, used = 0;
+  bool dry = false;
+  void begin_dry() {
+    dry = true;
+    used = 0;
+  }
+  int reserve() {  // after a dry carving: make room for it, then carve for real
+    const uint64_t need = used + 256;
+    dry = false;
+    used = 0;
+    if (need <= cap) return BT_OK;
+    if (base) cudaFreeAsync(base, s);
+    base = nullptr;
+    cap = 0;
+    const uint64_t want = need + need / 4;
+    cudaError_t e = cudaMallocAsync((void**)&base, want, s);
+    if (e != cudaSuccess) {
+      note_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
+      return e == cudaErrorMemoryAllocation ? BT_ENOMEM : BT_ECUDA;
+    }
+    cap = want;
+    return BT_OK;
+  }
+  template <class T>
+  T* take(uint64_t count) {
+    used = (used + 255) & ~255ull;
+    T* p = dry ? nullptr : (T*)(base + used);
+    used += (count ? count : 1) * sizeof(T);
+    return p;
+  }
+  void release() {
+    if (base) cudaFreeAsync(base, s);
+    base = nullptr;
+    cap = used = 0;
+  }
+};
+
 // Library-wide launch helpers.
 inline unsigned grid_for(uint64_t work, unsigned threads, unsigned cap = 152u * 32u) {
   uint64_t g = (work + threads - 1) / threads;
@@ -312,6 +357,9 @@ int prefix_fingerprints(const uint8_t* d_text, uint64_t n, uint64_t B, uint64_t 
 
 // Exclusive prefix sum of d_in[0, n) into d_out[0, n]; d_out[n] = total.
 int scan_u32(const uint32_t* d_in, uint32_t* d_out, uint64_t n, cudaStream_t s);
+// Same, with caller-provided scratch of scan_scratch_words(n) entries.
+int scan_u32(const uint32_t* d_in, uint32_t* d_out, uint64_t n, cudaStream_t s, uint32_t* agg);
+inline uint64_t scan_scratch_words(uint64_t n) { return (n + 1023) / 1024 + 1; }
 int scan_u64(const uint64_t* d_in, uint64_t* d_out, uint64_t n, cudaStream_t s);
 
 struct BuildCtx {
@@ -319,11 +367,13 @@ struct BuildCtx {
   const uint8_t* T;   // device text
   uint64_t* Hs;       // prefix fingerprints
   uint64_t* PB;       // B^k, k = 0..32
+  Arena arena;        // per-level scratch
   Status* st;         // device status
   Status* st_host;    // pinned mirror
   cudaStream_t s;
   uint64_t verify_bytes = 0, collisions = 0;
   int dense_scan = 0;  // probe every window (diagnostic) instead of the anchored scan
+  ~BuildCtx() { arena.release(); }
 };
 
 int build_levels(BuildCtx& ctx);

@@ -30,6 +30,7 @@
 //                     popcount prefix for rank;
 //   6. k_pointers     unmarked blocks -> (ptr, off) by binary search;
 //   7. k_children     the tau-way split of marked blocks into the next level.
+#include <chrono>
 #include <cstdio>
 #include <cstdlib>
 
@@ -720,14 +721,16 @@ __global__ void __launch_bounds__(256) k_verify(const uint8_t* __restrict__ T, c
 
 // 4c. Apply the pair verifications: a mismatch makes the pair a suspect key.
 __global__ void k_pair_apply(Geo g, const uint64_t* __restrict__ job_of,
-                             const unsigned int* __restrict__ mismatch, uint64_t* susp, LevelDev* ld,
-                             Status* status) {
+                             const unsigned int* __restrict__ mismatch, uint64_t* susp,
+                             unsigned long long* exlo, LevelDev* ld, Status* status) {
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k + 1 < g.c;
        k += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t id = job_of[k];
     if (id == kNone || !mismatch[id]) continue;
     atomicAdd(&status->collisions, 1ull);
-    susp[atomicAdd(&ld->nsusp, 1ull)] = k;
+    const unsigned long long i = atomicAdd(&ld->nsusp, 1ull);
+    susp[i] = k;
+    exlo[i] = g.st[k];  // the key's own start is an occurrence
   }
 }
 
@@ -774,14 +777,6 @@ __global__ void __launch_bounds__(256) k_exact_scan(M m, Geo g, uint64_t cpb, in
       if (eq) min_pos(&exlo[i], p);
     }
   }
-}
-
-__global__ void k_init_exlo(Geo g, const uint64_t* __restrict__ susp, unsigned long long* exlo,
-                            const LevelDev* ld) {
-  const uint64_t ns = ld->nsusp;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < ns;
-       i += (uint64_t)gridDim.x * blockDim.x)
-    exlo[i] = g.st[susp[i]];
 }
 
 __global__ void k_pair_exact_apply(Geo g, const uint64_t* __restrict__ susp,
@@ -857,14 +852,16 @@ __global__ void k_block_jobs(Geo g, const uint32_t* __restrict__ slotB,
 }
 
 __global__ void k_block_apply(Geo g, const uint64_t* __restrict__ job_of,
-                              const unsigned int* __restrict__ mismatch, uint64_t* susp, LevelDev* ld,
-                              Status* status) {
+                              const unsigned int* __restrict__ mismatch, uint64_t* susp,
+                              unsigned long long* exlo, LevelDev* ld, Status* status) {
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < g.c;
        k += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t id = job_of[k];
     if (id == kNone || !mismatch[id]) continue;
     atomicAdd(&status->collisions, 1ull);
-    susp[atomicAdd(&ld->nsusp, 1ull)] = k;
+    const unsigned long long i = atomicAdd(&ld->nsusp, 1ull);
+    susp[i] = k;
+    exlo[i] = g.st[k];  // the key's own start is an occurrence
   }
 }
 
@@ -955,6 +952,86 @@ __global__ void k_level_start(uint64_t c, uint64_t b, uint64_t* st) {
     st[k] = k * b;
 }
 
+struct InitArgs {
+  uint64_t* bkey;
+  uint32_t* brep;
+  unsigned long long* blo;
+  unsigned long long* maxpst;
+  uint64_t bcap;
+  uint64_t* pkey;
+  unsigned long long* plo;
+  uint64_t pcap;
+  unsigned int* mismatch;
+  uint64_t c;
+  AnchorSet* atab;
+  uint64_t acap;
+  uint32_t* bitmap;
+  uint64_t bwords;
+  uint32_t* secbits;
+  unsigned long long* qn;
+  LevelDev* ld;
+};
+
+// All per-level tables and flags in one launch: keys and minima to "empty",
+// counters and filters to zero.
+__global__ void k_level_init(InitArgs a) {
+  uint64_t top = a.bcap > a.pcap ? a.bcap : a.pcap;
+  if (a.c > top) top = a.c;
+  if (a.acap > top) top = a.acap;
+  if (a.bwords > top) top = a.bwords;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < top;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    if (i < a.bcap) {
+      a.bkey[i] = kNone;
+      a.brep[i] = 0xFFFFFFFFu;
+      a.blo[i] = kNone;
+      a.maxpst[i] = 0;
+    }
+    if (i < a.pcap) {
+      a.pkey[i] = kNone;
+      a.plo[i] = kNone;
+    }
+    if (i < a.c) a.mismatch[i] = 0;
+    if (a.atab && i < a.acap) {
+      a.atab[i].gram = kEmptyGram;
+      a.atab[i].offs = 0;
+      a.atab[i].maxst = 0;
+    }
+    if (a.bitmap && i < a.bwords) a.bitmap[i] = 0;
+    if (a.secbits && i < kSecBits / 32) a.secbits[i] = 0;
+    if (i == 0) {
+      LevelDev d;
+      d.fp_tail = kNone;
+      d.lo_tail = kNone;
+      d.lo_tailpair = kNone;
+      d.pretail_slot = 0xFFFFFFFFu;
+      d.npairs = 0;
+      d.njobs = 0;
+      d.nsusp = 0;
+      d.anchorless = 0;
+      d.tail_anchorless = 0;
+      d.tail_gram = 0xFFFFFFFFu;
+      d.tail_a = 0xFFFFFFFFu;
+      d.cands = 0;
+      d.hits = 0;
+      *a.ld = d;
+      if (a.qn) *a.qn = 0;
+    }
+  }
+}
+
+// Between the pair and the block verification: empty the job list again.
+__global__ void k_reset_jobs(unsigned int* mismatch, uint64_t c, LevelDev* ld) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < c;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    mismatch[i] = 0;
+    if (i == 0) {
+      ld->njobs = 0;
+      ld->nsusp = 0;
+    }
+  }
+}
+
 // Gram length 16 (at most half a block): long enough that a gram is rare
 // even over small or skewed alphabets, so few keys share an anchor gram;
 // anchor range W <= 64; selection density 2^-sbits chosen so that
@@ -997,7 +1074,6 @@ struct LevelWork {
 template <class M>
 int exact_pass(const M& m, const Geo& g, uint64_t cpb, int pair, LevelWork& W, cudaStream_t s) {
   const unsigned T = 256;
-  BT_LAUNCH(k_init_exlo<<<grid_for(g.c, T), T, 0, s>>>(g, W.susp, W.exlo, W.ld));
   BT_LAUNCH(k_exact_scan<M><<<grid_for(g.c * cpb, T), T, 0, s>>>(m, g, cpb, pair, W.fpB, W.susp, W.exlo, W.ld));
   BT_CUDA(cudaGetLastError());
   return BT_OK;
@@ -1030,96 +1106,113 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
   const uint64_t cpb = (b + kScanQ - 1) / kScanQ;
   const uint64_t bcap = pow2_at_least(2 * c), pcap = pow2_at_least(2 * c);
 
-  Scratch sc(s);
-  LevelWork W;
-  BT_TRY(sc.alloc(&W.fpB, c));
-  BT_TRY(sc.alloc(&W.slotB, c));
-  BT_TRY(sc.alloc(&W.slotP, c));
-  BT_TRY(sc.alloc(&W.pm, c));
-  BT_TRY(sc.alloc(&W.plo_k, c));
-  BT_TRY(sc.alloc(&W.job_of, c));
-  BT_TRY(sc.alloc(&W.susp, c));
-  BT_TRY(sc.alloc(&W.exlo, c));
-  BT_TRY(sc.alloc(&W.jobs, c));
-  BT_TRY(sc.alloc(&W.mismatch, c));
-  BT_TRY(sc.alloc(&W.bkey, bcap));
-  BT_TRY(sc.alloc(&W.brep, bcap));
-  BT_TRY(sc.alloc(&W.blo, bcap));
-  BT_TRY(sc.alloc(&W.pkey, pcap));
-  BT_TRY(sc.alloc(&W.plo, pcap));
-  BT_TRY(sc.alloc(&W.maxpst, bcap));
-  BT_TRY(sc.alloc(&W.ld, 1));
-  const uint64_t words = (c + 31) / 32;
-  BT_TRY(sc.alloc(&W.wpop, words));
-  // Persistent level arrays.
-  BT_CUDA(cudaMallocAsync(&v.mw, words * sizeof(uint32_t) + 4, s));
-  BT_CUDA(cudaMallocAsync(&v.mr, (words + 1) * sizeof(uint32_t), s));
-  BT_CUDA(cudaMallocAsync(&v.ptr, c * sizeof(uint32_t) + 4, s));
-  BT_CUDA(cudaMallocAsync(&v.off, c * sizeof(uint64_t) + 8, s));
-  BT_CUDA(cudaMallocAsync(&v.lo, c * sizeof(uint64_t) + 8, s));
-
-  BT_CUDA(cudaMemsetAsync(W.bkey, 0xFF, bcap * sizeof(uint64_t), s));
-  BT_CUDA(cudaMemsetAsync(W.brep, 0xFF, bcap * sizeof(uint32_t), s));
-  BT_CUDA(cudaMemsetAsync(W.blo, 0xFF, bcap * sizeof(uint64_t), s));
-  BT_CUDA(cudaMemsetAsync(W.pkey, 0xFF, pcap * sizeof(uint64_t), s));
-  BT_CUDA(cudaMemsetAsync(W.plo, 0xFF, pcap * sizeof(uint64_t), s));
-  BT_CUDA(cudaMemsetAsync(W.maxpst, 0, bcap * sizeof(uint64_t), s));
-  BT_CUDA(cudaMemsetAsync(W.ld, 0xFF, sizeof(LevelDev), s));
-  BT_CUDA(cudaMemsetAsync(&W.ld->npairs, 0, sizeof(unsigned int), s));
-  BT_CUDA(cudaMemsetAsync(&W.ld->njobs, 0, 2 * sizeof(unsigned long long), s));
-  BT_CUDA(cudaMemsetAsync(&W.ld->anchorless, 0, 2 * sizeof(unsigned int), s));
-  BT_CUDA(cudaMemsetAsync(&W.ld->cands, 0, 2 * sizeof(unsigned long long), s));
-  BT_CUDA(cudaMemsetAsync(W.mismatch, 0, c * sizeof(unsigned int), s));
-
   const unsigned T = 256;
   const unsigned gc = grid_for(c, T);
-  BT_LAUNCH(k_block_fp<M><<<gc, T, 0, s>>>(m, g, W.fpB, W.slotB, W.bkey, bcap - 1, W.brep, W.ld, ctx.st));
-  BT_LAUNCH(k_pair_insert<<<gc, T, 0, s>>>(g, W.slotB, W.slotP, W.pkey, pcap - 1, W.maxpst, W.ld,
-                                           ctx.st));
-  if (ctx.dense_scan) {
-    ProfScope ps("window_scan", s, (c - 1) * b + (len_last < b ? len_last : b));
-    BT_LAUNCH(k_scan<M><<<grid_for(c * cpb, T), T, 0, s>>>(m, g, cpb, W.bkey, bcap - 1, W.blo, W.pkey,
-                                                            pcap - 1, W.plo, W.ld, 0));
-  } else {
-    const GramP gp = choose_gram(b, r, t->S);
-    const uint64_t acap = pow2_at_least(2 * (c + 2));
+  const uint64_t words = (c + 31) / 32;
+  const bool anchored = !ctx.dense_scan;
+  const GramP gp = choose_gram(b, r, t->S);
+  const uint64_t acap = anchored ? pow2_at_least(2 * (c + 2)) : 0;
+  GramP gq = gp;
+  uint64_t bwords = 0;
+  if (anchored) {
     uint64_t fb = pow2_at_least(16 * (c + 2));
     uint32_t fbits = 0;
     while ((1ull << fbits) < fb) fbits++;
     if (fbits < 12) fbits = 12;
     if (fbits + gp.sbits > 32) fbits = 32 - gp.sbits;
-    GramP gq = gp;
     gq.fbits = fbits;
-    const uint64_t bwords = (1ull << fbits) / 32;
-    AnchorSet* atab;
-    uint32_t *bitmap, *secbits;
-    BT_TRY(sc.alloc(&atab, acap));
-    BT_TRY(sc.alloc(&bitmap, bwords));
-    BT_TRY(sc.alloc(&secbits, kSecBits / 32));
-    BT_CUDA(cudaMemsetAsync(atab, 0xFF, acap * sizeof(AnchorSet), s));
-    BT_CUDA(cudaMemsetAsync(bitmap, 0, bwords * 4, s));
-    BT_CUDA(cudaMemsetAsync(secbits, 0, kSecBits / 8, s));
-    BT_LAUNCH(k_clear_offs<<<grid_for(acap, T), T, 0, s>>>(atab, acap));
+    bwords = (1ull << fbits) / 32;
+  }
+  // Candidate queue: a few candidates per covered window is plenty; more
+  // are tested inline by the scan.
+  const uint64_t cov_l = (c - 1) * b + (len_last < b ? len_last : b);
+  uint64_t qcap = cov_l / 2 + 4096;
+  if (qcap > (64ull << 20)) qcap = 64ull << 20;
+
+  // Scratch: carved from the build's arena (a dry carving sizes it).
+  Arena& A = ctx.arena;
+  LevelWork W;
+  AnchorSet* atab = nullptr;
+  uint32_t *bitmap = nullptr, *secbits = nullptr, *sagg = nullptr;
+  Cand* q = nullptr;
+  unsigned long long* qn = nullptr;
+  auto carve = [&]() {
+    W.fpB = A.take<uint64_t>(c);
+    W.slotB = A.take<uint32_t>(c);
+    W.slotP = A.take<uint32_t>(c);
+    W.pm = A.take<uint8_t>(c);
+    W.plo_k = A.take<uint64_t>(c);
+    W.job_of = A.take<uint64_t>(c);
+    W.susp = A.take<uint64_t>(c);
+    W.exlo = A.take<unsigned long long>(c);
+    W.jobs = A.take<Job>(c);
+    W.mismatch = A.take<unsigned int>(c);
+    W.bkey = A.take<uint64_t>(bcap);
+    W.brep = A.take<uint32_t>(bcap);
+    W.blo = A.take<unsigned long long>(bcap);
+    W.maxpst = A.take<unsigned long long>(bcap);
+    W.pkey = A.take<uint64_t>(pcap);
+    W.plo = A.take<unsigned long long>(pcap);
+    W.ld = A.take<LevelDev>(1);
+    W.wpop = A.take<uint32_t>(words);
+    sagg = A.take<uint32_t>(scan_scratch_words(words));
+    if (anchored) {
+      atab = A.take<AnchorSet>(acap);
+      bitmap = A.take<uint32_t>(bwords);
+      secbits = A.take<uint32_t>(kSecBits / 32);
+      q = A.take<Cand>(qcap);
+      qn = A.take<unsigned long long>(1);
+    }
+  };
+  A.begin_dry();
+  carve();
+  BT_TRY(A.reserve());
+  carve();
+
+  // Persistent level arrays: one allocation, owned by the level.
+  {
+    auto al = [](uint64_t x) { return (x + 255) & ~255ull; };
+    const uint64_t o_mw = 0, o_mr = o_mw + al(words * 4 + 4), o_ptr = o_mr + al((words + 1) * 4),
+                   o_off = o_ptr + al(c * 4 + 4), o_lo = o_off + al(c * 8 + 8), total = o_lo + al(c * 8 + 8);
+    char* mem;
+    BT_CUDA(cudaMallocAsync((void**)&mem, total, s));
+    v.owned.push_back(mem);
+    v.mw = (uint32_t*)(mem + o_mw);
+    v.mr = (uint32_t*)(mem + o_mr);
+    v.ptr = (uint32_t*)(mem + o_ptr);
+    v.off = (uint64_t*)(mem + o_off);
+    v.lo = (uint64_t*)(mem + o_lo);
+  }
+
+  InitArgs ia{W.bkey, W.brep, W.blo, W.maxpst, bcap, W.pkey, W.plo, pcap, W.mismatch, c,
+              atab, acap, bitmap, bwords, secbits, qn, W.ld};
+  {
+    uint64_t top = bcap > acap ? bcap : acap;
+    if (bwords > top) top = bwords;
+    BT_LAUNCH(k_level_init<<<grid_for(top, T), T, 0, s>>>(ia));
+  }
+  BT_LAUNCH(k_block_fp<M><<<gc, T, 0, s>>>(m, g, W.fpB, W.slotB, W.bkey, bcap - 1, W.brep, W.ld, ctx.st));
+  BT_LAUNCH(k_pair_insert<<<gc, T, 0, s>>>(g, W.slotB, W.slotP, W.pkey, pcap - 1, W.maxpst, W.ld,
+                                           ctx.st));
+  if (!anchored) {
+    ProfScope ps("window_scan", s, cov_l);
+    BT_LAUNCH(k_scan<M><<<grid_for(c * cpb, T), T, 0, s>>>(m, g, cpb, W.bkey, bcap - 1, W.blo, W.pkey,
+                                                            pcap - 1, W.plo, W.ld, 0));
+  } else {
     BT_LAUNCH(k_anchor_keys<<<gc, T, 0, s>>>(g, gq, W.slotB, atab, (uint32_t)(acap - 1), bitmap, secbits,
                                              W.ld, ctx.st));
-    // Candidate queue: a few candidates per covered window is plenty; more
-    // are tested inline by the scan.
-    const uint64_t cov_l = (c - 1) * b + (len_last < b ? len_last : b);
-    uint64_t qcap = cov_l / 2 + 4096;
-    if (qcap > (64ull << 20)) qcap = 64ull << 20;
-    Cand* q;
-    unsigned long long* qn;
-    BT_TRY(sc.alloc(&q, qcap));
-    BT_TRY(sc.alloc(&qn, 1));
-    BT_CUDA(cudaMemsetAsync(qn, 0, sizeof(unsigned long long), s));
     ScanCtx<M> C{m, g, W.bkey, bcap - 1, W.blo, W.pkey, pcap - 1, W.plo, W.ld, 0, 0, W.maxpst, q, qn, qcap};
     const uint64_t cpa = (b + kAnchorQ - 1) / kAnchorQ;
     const uint32_t bm_smem = bwords <= kSmemBitmapWords ? (uint32_t)bwords : 0;
     const size_t smem = (kSecBits / 32 + bm_smem) * 4 + (size_t)kScanThreads * kSlotBytes;
-    BT_CUDA(cudaFuncSetAttribute(k_scan_anchor<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(((size_t)kSecBits / 32 + kSmemBitmapWords) * 4 +
-                                       (size_t)kScanThreads * kSlotBytes)));
-    ProfScope ps("window_scan", s, (c - 1) * b + (len_last < b ? len_last : b));
+    static bool attr_set = false;
+    if (!attr_set) {
+      BT_CUDA(cudaFuncSetAttribute(k_scan_anchor<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(((size_t)kSecBits / 32 + kSmemBitmapWords) * 4 +
+                                         (size_t)kScanThreads * kSlotBytes)));
+      attr_set = true;
+    }
+    ProfScope ps("window_scan", s, cov_l);
     BT_LAUNCH(k_scan_anchor<M><<<grid_for(c * cpa, kScanThreads, 152 * 8), kScanThreads, smem, s>>>(
         C, gq, cpa, atab, (uint32_t)(acap - 1), bitmap, bm_smem, secbits));
     BT_LAUNCH(k_candidates<M><<<152 * 16, 256, 0, s>>>(C));
@@ -1133,21 +1226,20 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
   const uint64_t ppj_pair = (2 * b + kPiece - 1) / kPiece;
   BT_LAUNCH(k_pair_jobs<<<gc, T, 0, s>>>(g, W.slotP, W.plo, W.plo_k, W.pm, W.jobs, W.job_of, W.ld, ctx.st));
   BT_LAUNCH(k_verify<<<grid_for(c * ppj_pair * 32, T), T, 0, s>>>(ctx.T, W.jobs, W.ld, ppj_pair, W.mismatch));
-  BT_LAUNCH(k_pair_apply<<<gc, T, 0, s>>>(g, W.job_of, W.mismatch, W.susp, W.ld, ctx.st));
+  BT_LAUNCH(k_pair_apply<<<gc, T, 0, s>>>(g, W.job_of, W.mismatch, W.susp, W.exlo, W.ld, ctx.st));
   BT_TRY(exact_pass(m, g, cpb, 1, W, s));
   BT_LAUNCH(k_pair_exact_apply<<<gc, T, 0, s>>>(g, W.susp, W.exlo, W.pm, W.plo_k, W.ld));
   BT_LAUNCH(k_mark<<<grid_for(words * 32, T), T, 0, s>>>(g, W.slotP, W.pm, v.mw, W.wpop));
   BT_CUDA(cudaGetLastError());
-  BT_TRY(scan_u32(W.wpop, v.mr, words, s));
+  BT_TRY(scan_u32(W.wpop, v.mr, words, s, sagg));
 
   // Blocks: leftmost occurrences, verified; pointers.
-  BT_CUDA(cudaMemsetAsync(&W.ld->njobs, 0, 2 * sizeof(unsigned long long), s));
-  BT_CUDA(cudaMemsetAsync(W.mismatch, 0, c * sizeof(unsigned int), s));
+  BT_LAUNCH(k_reset_jobs<<<gc, T, 0, s>>>(W.mismatch, c, W.ld));
   const uint64_t ppj_blk = (b + kPiece - 1) / kPiece;
   BT_LAUNCH(k_block_jobs<<<gc, T, 0, s>>>(g, W.slotB, W.blo, v.mw, t->prune, v.lo, W.jobs, W.job_of, W.ld,
                                 ctx.st));
   BT_LAUNCH(k_verify<<<grid_for(c * ppj_blk * 32, T), T, 0, s>>>(ctx.T, W.jobs, W.ld, ppj_blk, W.mismatch));
-  BT_LAUNCH(k_block_apply<<<gc, T, 0, s>>>(g, W.job_of, W.mismatch, W.susp, W.ld, ctx.st));
+  BT_LAUNCH(k_block_apply<<<gc, T, 0, s>>>(g, W.job_of, W.mismatch, W.susp, W.exlo, W.ld, ctx.st));
   BT_TRY(exact_pass(m, g, cpb, 0, W, s));
   BT_LAUNCH(k_block_exact_apply<<<gc, T, 0, s>>>(W.susp, W.exlo, v.lo, W.ld));
   BT_LAUNCH(k_pointers<<<gc, T, 0, s>>>(g, v.mw, v.lo, v.ptr, v.off, ctx.st));
@@ -1168,6 +1260,7 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
     nx.c = ctx.st_host->next_c;
     if (nx.c == 0) return BT_EINTERNAL;
     BT_CUDA(cudaMallocAsync(&nx.st, nx.c * sizeof(uint64_t), s));
+    nx.owned.push_back(nx.st);
     BT_LAUNCH(k_children<<<grid_for(c * v.arity, T), T, 0, s>>>(g, v.mw, v.mr, v.arity, bn, nx.st));
     BT_CUDA(cudaGetLastError());
   } else {
@@ -1201,11 +1294,19 @@ int all_levels(const M& m, BuildCtx& ctx) {
   Level& r = t->lv[0];
   r.c = (t->n + r.b - 1) / r.b;
   BT_CUDA(cudaMallocAsync(&r.st, r.c * sizeof(uint64_t), ctx.s));
+  r.owned.push_back(r.st);
   BT_LAUNCH(k_level_start<<<grid_for(r.c, 256), 256, 0, ctx.s>>>(r.c, r.b, r.st));
   uint64_t last_start = (r.c - 1) * r.b;
+  const bool trace = getenv("BT_TRACE") != nullptr;
   for (uint32_t l = 0; l < t->L; l++) {
+    auto h0 = std::chrono::steady_clock::now();
     BT_TRY(level_pass(m, ctx, l, last_start));
     last_start = ctx.st_host->last_start;
+    if (trace) {
+      auto h1 = std::chrono::steady_clock::now();
+      fprintf(stderr, "bt-trace level %u c=%llu host %.3f ms\n", l, (unsigned long long)t->lv[l].c,
+              std::chrono::duration<double, std::milli>(h1 - h0).count());
+    }
   }
   return BT_OK;
 }

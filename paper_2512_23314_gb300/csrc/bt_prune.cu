@@ -115,44 +115,94 @@ __global__ void k_indegree(PView v, const uint32_t* __restrict__ state, const ui
 }
 
 __global__ void k_round0(PView v, uint32_t* __restrict__ state, const uint32_t* __restrict__ indeg,
-                         uint32_t* __restrict__ dround) {
+                         uint32_t* __restrict__ dround, unsigned long long* prog) {
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < v.c;
        k += (uint64_t)gridDim.x * blockDim.x) {
     if (state[k] == UNDEC && indeg[k] == 0) {
       state[k] = PRUNED;
       dround[k] = 0;
+      atomicAdd(&prog[0], 1ull);
     }
   }
 }
 
-// One frontier round: candidates decided in round r-1 inform their targets.
+// Per-level scratch to its initial values in one launch.
+__global__ void k_prune_init(uint8_t* hit_v, uint8_t* hit2, uint64_t nv, uint8_t* tgt_w, uint8_t* gone,
+                             uint64_t nw, uint32_t* indeg, unsigned long long* prog) {
+  const uint64_t top = (nv > nw ? nv : nw) + 1;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < top;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    if (i <= nv) {
+      hit_v[i] = 0;
+      hit2[i] = 0;
+    }
+    if (i < nv) indeg[i] = 0;
+    if (i <= nw) {
+      tgt_w[i] = 0;
+      gone[i] = 0;
+    }
+    if (i < 4) prog[i] = 0;
+  }
+}
+
+// One frontier round for candidate k: if k was decided in round r-1, it
+// informs its targets (a pruned attacker keeps its target; a kept attacker
+// lowers the target's count of undecided attackers, and at zero the target
+// is pruned).  Decisions of round r are counted in prog[r % 3].
+__device__ __forceinline__ void round_step(const PView& v, uint32_t* state, uint32_t* indeg,
+                                           uint32_t* dround, const uint64_t* __restrict__ t1,
+                                           const uint64_t* __restrict__ t2, uint32_t r,
+                                           unsigned long long* prog, uint64_t k) {
+  if (dround[k] != r - 1) return;
+  const uint32_t sk = state[k];
+  for (int e = 0; e < 2; e++) {
+    const uint64_t t = e == 0 ? t1[k] : t2[k];
+    if (t == kNone || state[t] == NOTCAND) continue;
+    uint32_t target = 0;
+    if (sk == PRUNED) {
+      target = KEPT;
+    } else if (atomicSub(&indeg[t], 1u) == 1u) {
+      target = PRUNED;
+    }
+    if (target && atomicCAS(&state[t], (uint32_t)UNDEC, target) == UNDEC) {
+      dround[t] = r;
+      atomicAdd(&prog[r % 3], 1ull);
+    }
+  }
+}
+
+// Round r over all candidates.  A round after one that decided nothing has
+// nothing to do (the decided set is a fixed point) and returns at once.
 __global__ void k_round(PView v, uint32_t* state, uint32_t* indeg, uint32_t* dround,
                         const uint64_t* __restrict__ t1, const uint64_t* __restrict__ t2, uint32_t r,
-                        unsigned long long* progress) {
+                        unsigned long long* prog) {
+  if (*(volatile unsigned long long*)&prog[(r - 1) % 3] == 0) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) prog[(r + 1) % 3] = 0;
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < v.c;
-       k += (uint64_t)gridDim.x * blockDim.x) {
-    if (dround[k] != r - 1) continue;
-    uint32_t sk = state[k];
-    for (int e = 0; e < 2; e++) {
-      uint64_t t = e == 0 ? t1[k] : t2[k];
-      if (t == kNone || state[t] == NOTCAND) continue;
-      uint32_t target = 0;
-      if (sk == PRUNED) {
-        target = KEPT;
-      } else if (atomicSub(&indeg[t], 1u) == 1u) {
-        target = PRUNED;
-      }
-      if (target && atomicCAS(&state[t], (uint32_t)UNDEC, target) == UNDEC) {
-        dround[t] = r;
-        atomicAdd(progress, 1ull);
-      }
-    }
+       k += (uint64_t)gridDim.x * blockDim.x)
+    round_step(v, state, indeg, dround, t1, t2, r, prog, k);
+}
+
+// Rounds r0, r0+1, ... in one CTA until a round decides nothing or the
+// bound is reached (deep dependency chains after the multi-CTA rounds).
+__global__ void k_rounds_tail(PView v, uint32_t* state, uint32_t* indeg, uint32_t* dround,
+                              const uint64_t* __restrict__ t1, const uint64_t* __restrict__ t2,
+                              uint32_t r0, uint32_t rmax, unsigned long long* prog) {
+  for (uint32_t r = r0; r < rmax; r++) {
+    __syncthreads();
+    if (*(volatile unsigned long long*)&prog[(r - 1) % 3] == 0) return;
+    if (threadIdx.x == 0) prog[(r + 1) % 3] = 0;
+    for (uint64_t k = threadIdx.x; k < v.c; k += blockDim.x)
+      round_step(v, state, indeg, dround, t1, t2, r, prog, k);
+    __threadfence_block();
   }
 }
 
-// Right-to-left finish for candidates still undecided after the rounds.
+// Right-to-left finish for candidates still undecided after the bound.
 __global__ void k_finish_serial(PView v, uint32_t* state, const uint64_t* __restrict__ t1,
-                                const uint64_t* __restrict__ t2, uint8_t* hit) {
+                                const uint64_t* __restrict__ t2, uint8_t* hit,
+                                const unsigned long long* und) {
+  if (*und == 0) return;
   for (uint64_t k = v.c; k-- > 0;) {
     uint32_t s = state[k];
     if (s == UNDEC) {
@@ -257,67 +307,65 @@ int prune_tree(BuildCtx& ctx, uint64_t max_rounds) {
   cudaStream_t s = ctx.s;
   const unsigned T = 256;
   if (max_rounds == 0) max_rounds = 4096;
+  const uint32_t multi_rounds = 24;  // multi-CTA rounds before the one-CTA tail
   for (int l = (int)t->L - 2; l >= 0; l--) {
     Level& v = t->lv[l];
     Level& w = t->lv[l + 1];
     const int w_last = l + 1 == (int)t->L - 1;
-    Scratch sc(s);
-    uint8_t *hit_v, *tgt_w, *gone, *hit2;
-    uint32_t* state;
-    uint64_t *t1, *t2;
-    uint32_t *indeg, *dround;
-    unsigned long long* cnt;
-    BT_TRY(sc.alloc(&hit_v, v.c + 1));
-    BT_TRY(sc.alloc(&hit2, v.c + 1));
-    BT_TRY(sc.alloc(&tgt_w, w.c + 1));
-    BT_TRY(sc.alloc(&state, v.c + 1));
-    BT_TRY(sc.alloc(&gone, w.c + 1));
-    BT_TRY(sc.alloc(&t1, v.c));
-    BT_TRY(sc.alloc(&t2, v.c));
-    BT_TRY(sc.alloc(&indeg, v.c));
-    BT_TRY(sc.alloc(&dround, v.c));
-    BT_TRY(sc.alloc(&cnt, 2));
-    BT_CUDA(cudaMemsetAsync(hit_v, 0, v.c + 1, s));
-    BT_CUDA(cudaMemsetAsync(hit2, 0, v.c + 1, s));
-    BT_CUDA(cudaMemsetAsync(tgt_w, 0, w.c + 1, s));
-    BT_CUDA(cudaMemsetAsync(gone, 0, w.c + 1, s));
-    BT_CUDA(cudaMemsetAsync(indeg, 0, v.c * sizeof(uint32_t), s));
+    const uint64_t words = (v.c + 31) / 32;
+    Arena& A = ctx.arena;
+    uint8_t *hit_v = nullptr, *tgt_w = nullptr, *gone = nullptr, *hit2 = nullptr;
+    uint32_t *state = nullptr, *indeg = nullptr, *dround = nullptr, *wpop = nullptr, *sagg = nullptr;
+    uint64_t *t1 = nullptr, *t2 = nullptr, *keep = nullptr, *nidx = nullptr;
+    uint32_t* sagg2 = nullptr;
+    unsigned long long* prog = nullptr;
+    auto carve = [&]() {
+      hit_v = A.take<uint8_t>(v.c + 1);
+      hit2 = A.take<uint8_t>(v.c + 1);
+      tgt_w = A.take<uint8_t>(w.c + 1);
+      gone = A.take<uint8_t>(w.c + 1);
+      state = A.take<uint32_t>(v.c + 1);
+      t1 = A.take<uint64_t>(v.c);
+      t2 = A.take<uint64_t>(v.c);
+      indeg = A.take<uint32_t>(v.c);
+      dround = A.take<uint32_t>(v.c);
+      prog = A.take<unsigned long long>(4);
+      wpop = A.take<uint32_t>(words);
+      sagg = A.take<uint32_t>(scan_scratch_words(words));
+      keep = A.take<uint64_t>(w.c);
+      nidx = A.take<uint64_t>(w.c + 1);
+      sagg2 = A.take<uint32_t>(scan_scratch_words((w.c + 31) / 32));
+    };
+    A.begin_dry();
+    carve();
+    BT_TRY(A.reserve());
+    carve();
     PView pv = view_of(t, v), pw = view_of(t, w);
+    const uint64_t top = (v.c > w.c ? v.c : w.c) + 1;
+    BT_LAUNCH(k_prune_init<<<grid_for(top, T), T, 0, s>>>(hit_v, hit2, v.c, tgt_w, gone, w.c, indeg, prog));
     BT_LAUNCH(k_flag_targets<<<grid_for(v.c, T), T, 0, s>>>(pv, hit_v));
     BT_LAUNCH(k_flag_targets<<<grid_for(w.c, T), T, 0, s>>>(pw, tgt_w));
     BT_LAUNCH(k_candidates<<<grid_for(v.c, T), T, 0, s>>>(pv, pw, w_last, v.arity, hit_v, tgt_w, state, t1, t2,
                                                   ctx.st));
     BT_LAUNCH(k_indegree<<<grid_for(v.c, T), T, 0, s>>>(pv, state, t1, t2, indeg, dround));
-    BT_LAUNCH(k_round0<<<grid_for(v.c, T), T, 0, s>>>(pv, state, indeg, dround));
+    BT_LAUNCH(k_round0<<<grid_for(v.c, T), T, 0, s>>>(pv, state, indeg, dround, prog));
+    // Frontier rounds without host round trips: multi-CTA rounds that return
+    // at once after the fixed point, then one CTA for deep chains, then (only
+    // if the bound was hit) the single-thread right-to-left finish.
+    const uint32_t rmax = (uint32_t)(max_rounds < 0xFFFFFFF0u ? max_rounds : 0xFFFFFFF0u);
+    uint32_t r = 1;
+    for (; r <= multi_rounds && r < rmax; r++)
+      BT_LAUNCH(k_round<<<grid_for(v.c, T), T, 0, s>>>(pv, state, indeg, dround, t1, t2, r, prog));
+    BT_LAUNCH(k_rounds_tail<<<1, 1024, 0, s>>>(pv, state, indeg, dround, t1, t2, r, rmax, prog));
+    BT_LAUNCH(k_count_undecided<<<grid_for(v.c, T), T, 0, s>>>(pv, state, prog + 3));
+    BT_LAUNCH(k_finish_serial<<<1, 1, 0, s>>>(pv, state, t1, t2, hit2, prog + 3));
     BT_CUDA(cudaGetLastError());
-    // Frontier rounds, checked every 8 rounds.
-    uint64_t r = 1;
-    for (;;) {
-      for (int i = 0; i < 8; i++, r++)
-        BT_LAUNCH(k_round<<<grid_for(v.c, T), T, 0, s>>>(pv, state, indeg, dround, t1, t2, (uint32_t)r, cnt + 1));
-      BT_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
-      BT_LAUNCH(k_count_undecided<<<grid_for(v.c, T), T, 0, s>>>(pv, state, cnt));
-      unsigned long long und = 0;
-      BT_CUDA(cudaMemcpyAsync(&und, cnt, sizeof(und), cudaMemcpyDeviceToHost, s));
-      BT_CUDA(cudaStreamSynchronize(s));
-      if (und == 0) break;
-      if (r > max_rounds) {
-        BT_LAUNCH(k_finish_serial<<<1, 1, 0, s>>>(pv, state, t1, t2, hit2));
-        break;
-      }
-    }
     t->lv[l].stats[BT_ST_FINAL_BLOCKS] = v.c;
     BT_LAUNCH(k_apply<<<grid_for(v.c, T), T, 0, s>>>(pv, v.arity, w.b, state, t1, v.ptr, v.off, gone));
-    uint32_t* wpop;
-    const uint64_t words = (v.c + 31) / 32;
-    BT_TRY(sc.alloc(&wpop, words));
     BT_LAUNCH(k_clear_marks<<<grid_for(words * 32, T), T, 0, s>>>(pv, state, wpop));
-    BT_TRY(scan_u32(wpop, v.mr, words, s));
+    BT_TRY(scan_u32(wpop, v.mr, words, s, sagg));
 
     // Compact the next level.
-    uint64_t *keep, *nidx;
-    BT_TRY(sc.alloc(&keep, w.c));
-    BT_TRY(sc.alloc(&nidx, w.c + 1));
     BT_LAUNCH(k_keep<<<grid_for(w.c, T), T, 0, s>>>(w.c, gone, keep));
     BT_TRY(scan_u64(keep, nidx, w.c, s));
     uint64_t c2 = 0;
@@ -328,24 +376,27 @@ int prune_tree(BuildCtx& ctx, uint64_t max_rounds) {
       uint32_t *ptr2, *mw2, *mr2, *wpop2;
       uint8_t* mk2;
       const uint64_t words2 = (c2 + 31) / 32;
-      BT_CUDA(cudaMallocAsync(&st2, c2 * sizeof(uint64_t) + 8, s));
-      BT_CUDA(cudaMallocAsync(&off2, c2 * sizeof(uint64_t) + 8, s));
-      BT_CUDA(cudaMallocAsync(&lo2, c2 * sizeof(uint64_t) + 8, s));
-      BT_CUDA(cudaMallocAsync(&ptr2, c2 * sizeof(uint32_t) + 4, s));
-      BT_CUDA(cudaMallocAsync(&mw2, words2 * sizeof(uint32_t) + 4, s));
-      BT_CUDA(cudaMallocAsync(&mr2, (words2 + 1) * sizeof(uint32_t), s));
-      BT_TRY(sc.alloc(&mk2, c2 + 1));
-      BT_TRY(sc.alloc(&wpop2, words2 + 1));
+      auto al = [](uint64_t x) { return (x + 255) & ~255ull; };
+      const uint64_t o_st = 0, o_off = al(c2 * 8 + 8), o_lo = o_off + al(c2 * 8 + 8),
+                     o_ptr = o_lo + al(c2 * 8 + 8), o_mw = o_ptr + al(c2 * 4 + 4),
+                     o_mr = o_mw + al(words2 * 4 + 4), total = o_mr + al((words2 + 1) * 4);
+      char* mem;
+      BT_CUDA(cudaMallocAsync((void**)&mem, total, s));
+      st2 = (uint64_t*)(mem + o_st);
+      off2 = (uint64_t*)(mem + o_off);
+      lo2 = (uint64_t*)(mem + o_lo);
+      ptr2 = (uint32_t*)(mem + o_ptr);
+      mw2 = (uint32_t*)(mem + o_mw);
+      mr2 = (uint32_t*)(mem + o_mr);
+      BT_CUDA(cudaMallocAsync((void**)&mk2, c2 + 8 + 4 * (words2 + 1), s));
+      wpop2 = (uint32_t*)(((uintptr_t)(mk2 + c2 + 1) + 3) & ~(uintptr_t)3);
       BT_LAUNCH(k_compact<<<grid_for(w.c, T), T, 0, s>>>(pw, gone, nidx, st2, mk2, ptr2, off2, lo2, ctx.st));
       BT_LAUNCH(k_pack_marks<<<grid_for(words2 * 32, T), T, 0, s>>>(c2, mk2, mw2, wpop2));
-      BT_TRY(scan_u32(wpop2, mr2, words2, s));
+      BT_TRY(scan_u32(wpop2, mr2, words2, s, sagg2));
       BT_CUDA(cudaGetLastError());
-      cudaFreeAsync(w.st, s);
-      cudaFreeAsync(w.off, s);
-      cudaFreeAsync(w.lo, s);
-      cudaFreeAsync(w.ptr, s);
-      cudaFreeAsync(w.mw, s);
-      cudaFreeAsync(w.mr, s);
+      cudaFreeAsync(mk2, s);
+      for (void* a : w.owned) cudaFreeAsync(a, s);
+      w.owned.assign(1, mem);
       w.st = st2;
       w.off = off2;
       w.lo = lo2;

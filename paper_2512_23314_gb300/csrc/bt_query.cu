@@ -306,10 +306,13 @@ int build_counters(BuildCtx& ctx) {
   const size_t smem = 8 * S * sizeof(unsigned int);
   for (int l = (int)t->L - 1; l >= 0; l--) {
     Level& v = t->lv[l];
-    BT_CUDA(cudaMallocAsync(&v.cnt, v.c * S * sizeof(uint32_t) + 4, s));
-    BT_CUDA(cudaMallocAsync(&v.pc, v.c * S * sizeof(uint32_t) + 4, s));
-    BT_CUDA(cudaMemsetAsync(v.cnt, 0, v.c * S * sizeof(uint32_t), s));
-    BT_CUDA(cudaMemsetAsync(v.pc, 0, v.c * S * sizeof(uint32_t), s));
+    const uint64_t half = ((v.c * S * sizeof(uint32_t) + 4) + 255) & ~255ull;
+    char* mem;
+    BT_CUDA(cudaMallocAsync((void**)&mem, 2 * half, s));
+    v.owned.push_back(mem);
+    v.cnt = (uint32_t*)mem;
+    v.pc = (uint32_t*)(mem + half);
+    BT_CUDA(cudaMemsetAsync(mem, 0, 2 * half, s));
     const uint64_t ppb = (v.b + kCountPiece - 1) / kCountPiece;
     const bool last = l + 1 == (int)t->L;
     CountJob J{v.st, v.ptr, v.off, v.mw, v.c, v.b, t->n, v.cnt, 0, 0, 0};

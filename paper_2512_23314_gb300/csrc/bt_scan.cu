@@ -228,6 +228,18 @@ int kr_prefix(const M& m, const uint8_t* T, uint64_t n, uint64_t B, uint64_t* Hs
 int scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, cudaStream_t s) {
   return scan_sum<uint32_t>(in, out, n, s);
 }
+int scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, cudaStream_t s, uint32_t* agg) {
+  if (n == 0) {
+    BT_CUDA(cudaMemsetAsync(out, 0, sizeof(uint32_t), s));
+    return BT_OK;
+  }
+  const uint64_t na = (n + kTile - 1) / kTile;
+  BT_LAUNCH(k_sum_local<uint32_t><<<(unsigned)na, kTile, 0, s>>>(in, out, n, agg));
+  BT_LAUNCH(k_sum_aggs<uint32_t><<<1, kTile, 0, s>>>(agg, na));
+  BT_LAUNCH(k_sum_add<uint32_t><<<(unsigned)na, kTile, 0, s>>>(out, n, agg));
+  BT_CUDA(cudaGetLastError());
+  return BT_OK;
+}
 int scan_u64(const uint64_t* in, uint64_t* out, uint64_t n, cudaStream_t s) {
   return scan_sum<uint64_t>(in, out, n, s);
 }
