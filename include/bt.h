@@ -71,9 +71,12 @@ typedef struct {
   uint32_t flags;              /* BT_FLAG_* (0 by default)                    */
 } bt_opts;
 
-/* flags: probe the table at every window position instead of the anchored
- * scan (a diagnostic; both give the same tree). */
-enum { BT_FLAG_DENSE_SCAN = 1 };
+/* flags: BT_FLAG_DENSE_SCAN probes the table at every window position instead
+ * of the anchored scan (a diagnostic; both give the same tree).
+ * BT_FLAG_TINY_QUEUE caps the anchored scan's queue of proposed windows at 64
+ * entries, so that nearly every level takes the overflow path, a second scan
+ * that tests the windows in place (a test hook; the same tree again). */
+enum { BT_FLAG_DENSE_SCAN = 1, BT_FLAG_TINY_QUEUE = 2 };
 
 void bt_opts_default(bt_opts* opts);
 

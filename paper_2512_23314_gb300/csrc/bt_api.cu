@@ -187,6 +187,7 @@ static int build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, 
   ctx.s = s;
   ctx.arena.s = s;
   ctx.dense_scan = (o.flags & BT_FLAG_DENSE_SCAN) ? 1 : 0;
+  ctx.tiny_queue = (o.flags & BT_FLAG_TINY_QUEUE) ? 1 : 0;
   BT_TRY(sc.alloc(&ctx.st, 1));
   BT_CUDA(cudaMemsetAsync(ctx.st, 0, sizeof(Status), s));
   BT_CUDA(cudaMallocHost(&ctx.st_host, sizeof(Status)));
@@ -200,17 +201,16 @@ static int build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, 
     BT_TRY(alphabet(dT, n, sigma, t, s));
   }
   tr.mark("setup+alphabet");
-  BT_TRY(sc.alloc(&ctx.Hs, n / kPrefixStride + 2));
   {
-    uint64_t pb[kPrefixStride + 1];
-    pb[0] = 1;
-    for (uint32_t k = 1; k <= kPrefixStride; k++)
-      pb[k] = t->q == Mersenne61::Q ? Mersenne61{}.mul(pb[k - 1], t->B) : SmallMod{t->q}.mul(pb[k - 1], t->B);
-    BT_TRY(sc.alloc(&ctx.PB, kPrefixStride + 1));
-    BT_CUDA(cudaMemcpyAsync(ctx.PB, pb, sizeof(pb), cudaMemcpyHostToDevice, s));
-    BT_CUDA(cudaStreamSynchronize(s));
+    // Prefix fingerprints at every position, for the whole construction; the
+    // stride-32 values are an intermediate step.
+    Scratch hs(s);
+    uint64_t* Hs;
+    BT_TRY(hs.alloc(&Hs, n / kPrefixStride + 2));
+    BT_TRY(sc.alloc(&ctx.H, n + 1));
+    BT_TRY(prefix_fingerprints(dT, n, t->B, t->q, Hs, s));
+    BT_TRY(expand_prefix(dT, n, t->B, t->q, Hs, ctx.H, s));
   }
-  BT_TRY(prefix_fingerprints(dT, n, t->B, t->q, ctx.Hs, s));
   {
     ProfScope ps("phase_levels", s, 0);
     BT_TRY(build_levels(ctx));

@@ -2,7 +2,8 @@
 //
 // Device data layout (one tree, all in HBM):
 //   text        u8[n]          the input (the caller's device buffer, or a copy)
-//   Hs          u64[n/32 + 1]  Karp-Rabin prefix fingerprints H(32 j) (section 2)
+//   H           u64[n + 1]     Karp-Rabin prefix fingerprints H(p) (section 2),
+//                              during construction only
 //   per level l (blocks in text order):
 //     st        u64[c]         block starts (multiples of b_l)
 //     mw        u32[ceil(c/32)] mark bits, bit k%32 of word k/32
@@ -86,66 +87,12 @@ __host__ __device__ inline uint64_t pow_mod(const M& m, uint64_t a, uint64_t e) 
   return r;
 }
 
-// Prefix fingerprint at an arbitrary position p: the stored H(32*floor(p/32))
-// extended by Horner over at most 31 bytes.
+// phi(p, p+len) = H(p+len) - H(p) * B^len  (BL = B^len), from the prefix
+// fingerprints H at every position (section 2): two loads and one product.
 template <class M>
-__device__ __forceinline__ uint64_t prefix_at(const M& m, const uint8_t* __restrict__ T,
-                                              const uint64_t* __restrict__ Hs, uint64_t B,
-                                              uint64_t p) {
-  uint64_t j = p / kPrefixStride;
-  uint64_t h = Hs[j];
-  for (uint64_t i = j * kPrefixStride; i < p; i++) h = m.add(m.mul(h, B), (uint64_t)T[i] + 1);
-  return h;
-}
-
-// phi(p, p+len) = H(p+len) - H(p) * B^len  (BL = B^len).
-template <class M>
-__device__ __forceinline__ uint64_t window_fp(const M& m, const uint8_t* __restrict__ T,
-                                              const uint64_t* __restrict__ Hs, uint64_t B,
-                                              uint64_t BL, uint64_t p, uint64_t len) {
-  return m.sub(prefix_at(m, T, Hs, B, p + len), m.mul(prefix_at(m, T, Hs, B, p), BL));
-}
-
-// Faster form of prefix_at for q = 2^61-1 with a table PB[k] = B^k, k <= 32:
-//   H(p) = H(32 j) * B^d + sum_{i<d} (T[32 j + i] + 1) * B^(d-1-i),  d = p - 32 j.
-// The sum is accumulated exactly in two 64-bit halves (products of a 9-bit
-// symbol with the low / high 32 bits of B^k) and reduced once.
-__device__ __forceinline__ uint64_t prefix_fast(const Mersenne61& m, const uint8_t* __restrict__ T,
-                                               const uint64_t* __restrict__ Hs,
-                                               const uint64_t* __restrict__ PB, uint64_t p) {
-  const uint64_t j = p / kPrefixStride;
-  const uint32_t d = (uint32_t)(p - j * kPrefixStride);
-  uint64_t h = Hs[j];
-  if (d == 0) return h;
-  const uint8_t* t = T + j * kPrefixStride;
-  uint64_t lo = 0, hi = 0;
-  for (uint32_t i = 0; i < d; i++) {
-    const uint64_t pw = PB[d - 1 - i];
-    const uint64_t c = (uint64_t)t[i] + 1;
-    lo += c * (uint32_t)pw;
-    hi += c * (uint32_t)(pw >> 32);
-  }
-  const uint64_t vlo = lo + (hi << 32);
-  const uint64_t vhi = (hi >> 32) + (vlo < lo ? 1 : 0);
-  uint64_t r = (vlo & Mersenne61::Q) + (vlo >> 61) + (vhi << 3);
-  r = (r & Mersenne61::Q) + (r >> 61);
-  r = r >= Mersenne61::Q ? r - Mersenne61::Q : r;
-  return m.add(m.mul(h, PB[d]), r);
-}
-
-__device__ __forceinline__ uint64_t prefix_fast(const SmallMod& m, const uint8_t* __restrict__ T,
-                                               const uint64_t* __restrict__ Hs,
-                                               const uint64_t* __restrict__ PB, uint64_t p) {
-  (void)PB;
-  return prefix_at(m, T, Hs, PB[1], p);
-}
-
-template <class M>
-__device__ __forceinline__ uint64_t window_fast(const M& m, const uint8_t* __restrict__ T,
-                                               const uint64_t* __restrict__ Hs,
-                                               const uint64_t* __restrict__ PB, uint64_t BL,
-                                               uint64_t p, uint64_t len) {
-  return m.sub(prefix_fast(m, T, Hs, PB, p + len), m.mul(prefix_fast(m, T, Hs, PB, p), BL));
+__device__ __forceinline__ uint64_t window_fast(const M& m, const uint64_t* __restrict__ H,
+                                               uint64_t BL, uint64_t p, uint64_t len) {
+  return m.sub(H[p + len], m.mul(H[p], BL));
 }
 
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
@@ -354,6 +301,9 @@ inline unsigned grid_for(uint64_t work, unsigned threads, unsigned cap = 152u * 
 // Host entry points implemented across the .cu files --------------------------
 int prefix_fingerprints(const uint8_t* d_text, uint64_t n, uint64_t B, uint64_t q,
                         uint64_t* d_Hs, cudaStream_t s);
+// H[p] for every p in [0, n] from the stride-32 values Hs (n/32 + 1 entries).
+int expand_prefix(const uint8_t* d_text, uint64_t n, uint64_t B, uint64_t q,
+                  const uint64_t* d_Hs, uint64_t* d_H, cudaStream_t s);
 
 // Exclusive prefix sum of d_in[0, n) into d_out[0, n]; d_out[n] = total.
 int scan_u32(const uint32_t* d_in, uint32_t* d_out, uint64_t n, cudaStream_t s);
@@ -365,14 +315,14 @@ int scan_u64(const uint64_t* d_in, uint64_t* d_out, uint64_t n, cudaStream_t s);
 struct BuildCtx {
   bt_tree* t;
   const uint8_t* T;   // device text
-  uint64_t* Hs;       // prefix fingerprints
-  uint64_t* PB;       // B^k, k = 0..32
+  uint64_t* H;        // prefix fingerprints at every position, n + 1 entries
   Arena arena;        // per-level scratch
   Status* st;         // device status
   Status* st_host;    // pinned mirror
   cudaStream_t s;
   uint64_t verify_bytes = 0, collisions = 0;
   int dense_scan = 0;  // probe every window (diagnostic) instead of the anchored scan
+  int tiny_queue = 0;  // test hook: a 64-entry candidate queue (forces the overflow path)
   ~BuildCtx() { arena.release(); }
 };
 

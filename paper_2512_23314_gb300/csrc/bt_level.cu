@@ -30,6 +30,8 @@
 //                     popcount prefix for rank;
 //   6. k_pointers     unmarked blocks -> (ptr, off) by binary search;
 //   7. k_children     the tau-way split of marked blocks into the next level.
+#include <atomic>
+#include <cmath>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -62,15 +64,16 @@ struct LevelDev {
   unsigned int tail_anchorless;     // tail key: 1 shorter than a gram, 2 no anchor
   unsigned int tail_gram;           // anchor gram of the tail key (remapped)
   unsigned int tail_a;              // its anchor offset
+  unsigned int far_end;             // 1 + the largest far anchor offset of a full-length key
   unsigned long long cands;         // windows proposed by anchors and filters
   unsigned long long hits;          // proposed windows whose fingerprint is a key's
+  unsigned int qover;               // some CTA's queue segment overflowed
 };
 
 struct Geo {
   const uint8_t* T;
   uint64_t n;
-  const uint64_t* Hs;
-  const uint64_t* PB;       // B^k, k <= 32
+  const uint64_t* H;        // prefix fingerprints at every position
   uint64_t B, Bb, Br, Bbr;  // B, B^b, B^r, B^(b+r)
   uint64_t c, b, r;         // blocks, block length, tail length (0: no short tail)
   const uint64_t* st;
@@ -147,7 +150,7 @@ __global__ void k_block_fp(M m, Geo g, uint64_t* __restrict__ fpB, uint32_t* __r
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < g.c;
        k += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t s = g.st[k], len = blen(g, k);
-    uint64_t fp = window_fast(m, g.T, g.Hs, g.PB, len == g.b ? g.Bb : g.Br, s, len);
+    uint64_t fp = window_fast(m, g.H, len == g.b ? g.Bb : g.Br, s, len);
     fpB[k] = fp;
     if (len == g.b) {
       uint32_t slot = tbl_insert(bkey, bmask, fp);
@@ -211,7 +214,7 @@ __global__ void __launch_bounds__(256) k_scan(M m, Geo g, uint64_t cpb,
     const uint64_t pend = (p0 + kScanQ < s + len) ? p0 + kScanQ : s + len;
     const uint64_t av = avail_end(g, k);
     if (!tail_only && p0 + g.b <= av) {
-      uint64_t fp = window_fast(m, g.T, g.Hs, g.PB, g.Bb, p0, g.b);
+      uint64_t fp = window_fast(m, g.H, g.Bb, p0, g.b);
       for (uint64_t p = p0; p < pend && p + g.b <= av; p++) {
         if (p > p0) {
           uint64_t out = (uint64_t)g.T[p - 1] + 1, in = (uint64_t)g.T[p + g.b - 1] + 1;
@@ -221,7 +224,7 @@ __global__ void __launch_bounds__(256) k_scan(M m, Geo g, uint64_t cpb,
         if (sl == kNoSlot) continue;
         min_pos(&blo[sl], p);
         if (p + 2 * g.b <= av) {
-          uint64_t fp2 = window_fast(m, g.T, g.Hs, g.PB, g.Bb, p + g.b, g.b);
+          uint64_t fp2 = window_fast(m, g.H, g.Bb, p + g.b, g.b);
           uint32_t s2 = tbl_find(bkey, bmask, fp2);
           if (s2 != kNoSlot) {
             uint32_t ps = tbl_find(pkey, pmask, ((uint64_t)sl << 32) | s2);
@@ -229,12 +232,12 @@ __global__ void __launch_bounds__(256) k_scan(M m, Geo g, uint64_t cpb,
           }
         }
         if (g.r && sl == pretail && p + g.b + g.r <= av &&
-            window_fast(m, g.T, g.Hs, g.PB, g.Br, p + g.b, g.r) == fp_tail)
+            window_fast(m, g.H, g.Br, p + g.b, g.r) == fp_tail)
           min_pos(&ld->lo_tailpair, p);
       }
     }
     if (g.r && p0 + g.r <= av) {
-      uint64_t fp = window_fast(m, g.T, g.Hs, g.PB, g.Br, p0, g.r);
+      uint64_t fp = window_fast(m, g.H, g.Br, p0, g.r);
       for (uint64_t p = p0; p < pend && p + g.r <= av; p++) {
         if (p > p0) {
           uint64_t out = (uint64_t)g.T[p - 1] + 1, in = (uint64_t)g.T[p + g.r - 1] + 1;
@@ -251,61 +254,61 @@ __global__ void __launch_bounds__(256) k_scan(M m, Geo g, uint64_t cpb,
 //
 // Probing the table at every window position costs a random memory access
 // per text byte.  Instead every window gets an anchor that depends only on its
-// content: the first position, among its first W, of a w-gram whose 32-bit
-// gram hash is "selected" (top sbits of a multiplicative mix are zero, density
-// 2^-sbits).  Every key is registered under its anchor gram: the anchor table
-// maps a gram to the set of offsets (a 64-bit mask) at which keys anchor on
-// it.  The scan rolls a 32-bit gram hash over the level (no 61-bit arithmetic
-// per byte); only at a selected gram that passes a bitmap filter does it read
-// the anchor table, and each offset a in the gram's mask proposes the window
-// at x - a, whose 61-bit fingerprint is looked up in the block table.  A
-// window equal to a key has the key's anchor (same gram, same offset), so it
-// is always proposed: the slot minima are the same as when probing every
-// window.  A key without an anchor in its first W grams can only be equal to a
-// window without one; such keys are registered by their first gram in a small
-// shared-memory filter, checked at every position only when such keys exist.
+// content: the first position of a w-gram whose mixed 32-bit gram hash is
+// "selected" (at most 2^(32-sbits) - 1, density 2^-sbits).  Every key is
+// registered under its anchor gram: the anchor table maps a gram to the set of
+// offsets (a 64-bit mask for offsets below W, plus one far offset) at which
+// keys anchor on it.  The scan rolls the 32-bit gram hash over the level (no
+// 61-bit arithmetic per byte) and only records the selected grams; a second
+// pass tests those against a bitmap filter, reads the anchor table for the
+// few that pass, and each offset a proposes the window at x - a, whose 61-bit
+// fingerprint is then looked up in the block table.  A window equal to a key
+// has the key's anchor (same gram, same offset), so it is always proposed: the
+// slot minima are the same as when probing every window.  A key without any
+// selected gram (or whose far offset clashes with another key's on the same
+// gram) is registered by its first gram in a small shared-memory filter that
+// is checked at every position only when such keys exist.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kAnchorQ = 128;        // window starts per thread
-constexpr uint32_t kAnchorWmax = 64;      // anchor search range
+constexpr uint32_t kAnchorQ = 128;        // gram positions per thread
+constexpr uint32_t kAnchorWmax = 64;      // near anchor range (bits of the offset mask)
+constexpr uint32_t kFarMax = 4096;        // far anchors are searched up to this offset
+constexpr uint32_t kNoFar = 0xFFFFFFFFu;
 constexpr uint32_t kEmptyGram = 0xFFFFFFFFu;
 constexpr uint32_t kFibMul = 0x9E3779B1u;
 constexpr uint32_t kScanThreads = 256;
-constexpr uint32_t kSlotBytes = 180;      // staging bytes per thread (45 words: 45 = 13 mod 32)
+constexpr uint32_t kSlotWords = 37;       // staging words per thread (37 is odd: no bank conflicts)
+constexpr uint32_t kRing = 32;            // selected grams remembered per thread
 constexpr uint32_t kSecBits = 4096;       // first-gram filter of keys without an anchor
 constexpr uint32_t kSmemBitmapWords = 8192;  // anchor bitmap kept in shared memory up to 32 KiB
 
 struct GramP {
-  uint32_t w;      // gram length
-  uint32_t W;      // anchor search range for full-length windows
-  uint32_t Wr;     // anchor search range for the short tail (0: none)
-  uint32_t sbits;  // selection: top sbits of the mixed gram are zero
-  uint32_t fbits;  // bitmap index bits
-  uint32_t rb;     // gram base (odd)
-  uint32_t rw;     // rb^w mod 2^32
+  uint32_t w;        // gram length
+  uint32_t W;        // near anchor range for full-length windows
+  uint32_t Wr;       // near anchor range for the short tail (0: no gram fits)
+  uint32_t sbits;    // selection density 2^-sbits
+  uint32_t sel_max;  // a mixed gram hash is selected iff it is <= sel_max
+  uint32_t fbits;    // bitmap index bits
+  uint32_t rb;       // gram base (odd)
+  uint32_t rw;       // rb^w mod 2^32
 };
 
 // gram -> offsets at which keys anchor on it.
 struct AnchorSet {
-  uint32_t gram;             // remapped gram hash (kEmptyGram: empty slot)
-  uint32_t pad;
-  unsigned long long offs;   // bit a: some key has its anchor at offset a
+  uint32_t gram;             // remapped mixed gram hash (kEmptyGram: empty slot)
+  uint32_t far;              // one anchor offset >= W (kNoFar: none)
+  unsigned long long offs;   // bit a: some key has its anchor at offset a < W
   unsigned long long maxst;  // largest start of a key anchored on this gram
 };
 
-__device__ __forceinline__ uint32_t gram_hash(const uint8_t* __restrict__ T, uint64_t x, uint32_t w,
-                                              uint32_t rb) {
-  uint32_t h = 0;
-  for (uint32_t i = 0; i < w; i++) h = h * rb + T[x + i];
-  return h;
+// The gram hash is a polynomial in rb over the symbols; its mixed value
+// (times an odd constant, a bijection) decides selection, the bitmap bit and
+// the table key.
+__device__ __forceinline__ uint32_t gram_mix(uint32_t gh) { return gh * kFibMul; }
+__device__ __forceinline__ uint32_t gram_bit(const GramP& gp, uint32_t mx) {
+  return (mx << gp.sbits) >> (32 - gp.fbits);
 }
-__device__ __forceinline__ bool gram_selected(const GramP& gp, uint32_t g) {
-  return gp.sbits == 0 || ((g * kFibMul) >> (32 - gp.sbits)) == 0;
-}
-__device__ __forceinline__ uint32_t gram_bit(const GramP& gp, uint32_t g) {
-  return ((g * kFibMul) << gp.sbits) >> (32 - gp.fbits);
-}
-// Gram hashes are remapped away from 0xFFFFFFFF, the empty marker.
-__device__ __forceinline__ uint32_t gram_key(uint32_t g) { return g == kEmptyGram ? kEmptyGram - 1 : g; }
+// Mixed hashes are remapped away from 0xFFFFFFFF, the empty marker.
+__device__ __forceinline__ uint32_t gram_key(uint32_t mx) { return mx == kEmptyGram ? kEmptyGram - 1 : mx; }
 __device__ __forceinline__ uint32_t gram_slot(uint32_t g, uint32_t mask) {
   g ^= g >> 16;
   g *= 0x7FEB352Du;
@@ -314,15 +317,7 @@ __device__ __forceinline__ uint32_t gram_slot(uint32_t g, uint32_t mask) {
   g ^= g >> 16;
   return g & mask;
 }
-__device__ __forceinline__ uint32_t sec_bit(uint32_t g) { return (g * 0x2545F491u) >> 20; }  // 12 bits
-
-__global__ void k_clear_offs(AnchorSet* atab, uint64_t cap) {
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < cap;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    atab[i].offs = 0;
-    atab[i].maxst = 0;
-  }
-}
+__device__ __forceinline__ uint32_t sec_bit(uint32_t mx) { return (mx * 0x2545F491u) >> 20; }  // 12 bits
 
 // Register the anchor of every key (every block and the tail).
 __global__ void k_anchor_keys(Geo g, GramP gp, const uint32_t* __restrict__ slotB, AnchorSet* atab,
@@ -343,43 +338,57 @@ __global__ void k_anchor_keys(Geo g, GramP gp, const uint32_t* __restrict__ slot
         continue;
       }
     }
-    const uint32_t g0 = gram_hash(g.T, s, gp.w, gp.rb);
-    uint32_t gh = g0, a = kNoSlot;
-    for (uint32_t o = 0; o < Wk; o++) {
+    // Gram positions of the key: [0, len - w]; the far search stops at kFarMax.
+    const uint64_t npos = len - gp.w + 1;
+    const uint32_t lim = (uint32_t)(npos < kFarMax ? npos : kFarMax);
+    uint32_t gh = 0;
+    for (uint32_t i = 0; i < gp.w; i++) gh = gh * gp.rb + g.T[s + i];
+    const uint32_t mx0 = gram_mix(gh);
+    uint32_t a = kNoSlot, mx = mx0;
+    for (uint32_t o = 0; o < lim; o++) {
       if (o > 0) gh = gh * gp.rb - (uint32_t)g.T[s + o - 1] * gp.rw + g.T[s + o + gp.w - 1];
-      if (gram_selected(gp, gh)) {
+      mx = gram_mix(gh);
+      if (mx <= gp.sel_max) {
         a = o;
         break;
       }
     }
-    if (a == kNoSlot) {  // no anchor: registered by its first gram
-      const uint32_t sb = sec_bit(g0);
+    const uint32_t gk = gram_key(mx);
+    bool sec = a == kNoSlot;
+    if (!sec && !tail) {
+      uint32_t h = gram_slot(gk, amask);
+      bool placed = false;
+      for (uint32_t it = 0; it <= amask && !placed; it++) {
+        const uint32_t cur = atomicCAS(&atab[h].gram, kEmptyGram, gk);
+        if (cur == kEmptyGram || cur == gk) {
+          placed = true;
+          if (a < Wk) {
+            atomicOr(&atab[h].offs, 1ull << a);
+          } else {
+            const uint32_t f = atomicCAS(&atab[h].far, kNoFar, a);
+            if (f != kNoFar && f != a) sec = true;  // another far offset holds the entry
+            else atomicMax(&ld->far_end, a + 1);
+          }
+          atomicMax(&atab[h].maxst, (unsigned long long)s);
+        } else {
+          h = (h + 1) & amask;
+        }
+      }
+      if (!placed) atomicExch(&status->error, 7ull);
+    }
+    if (sec) {  // no usable anchor: registered by its first gram
+      const uint32_t sb = sec_bit(mx0);
       atomicOr(&secbits[sb >> 5], 1u << (sb & 31));
       if (tail) ld->tail_anchorless = 2u;
       else ld->anchorless = 1u;
       continue;
     }
-    const uint32_t gk = gram_key(gh);
-    const uint32_t bit = gram_bit(gp, gh);
+    const uint32_t bit = gram_bit(gp, mx);
     atomicOr(&bitmap[bit >> 5], 1u << (bit & 31));
     if (tail) {
       ld->tail_gram = gk;
       ld->tail_a = a;
-      continue;
     }
-    uint32_t h = gram_slot(gk, amask);
-    bool placed = false;
-    for (uint32_t it = 0; it <= amask && !placed; it++) {
-      const uint32_t cur = atomicCAS(&atab[h].gram, kEmptyGram, gk);
-      if (cur == kEmptyGram || cur == gk) {
-        atomicOr(&atab[h].offs, 1ull << a);
-        atomicMax(&atab[h].maxst, (unsigned long long)s);
-        placed = true;
-      } else {
-        h = (h + 1) & amask;
-      }
-    }
-    if (!placed) atomicExch(&status->error, 7ull);
   }
 }
 
@@ -397,36 +406,42 @@ struct ScanCtx {
   uint32_t pretail;
   uint64_t fp_tail;
   const unsigned long long* maxpst;  // last pair start per first-block slot
-  struct Cand* q;                    // candidate windows for k_candidates
-  unsigned long long* qn;            // candidates appended (may exceed qcap)
-  uint64_t qcap;
+  struct Hit* q;                     // gram hits: one segment of `seg` entries per scan CTA
+  uint32_t* segn;                    // hits recorded by each scan CTA (may exceed seg)
+  uint32_t seg;
+  unsigned long long* qn;            // hits recorded in all
+  Status* status;                    // device-side invariant checks
 };
 
-// A proposed window: start p, the block k whose scan thread proposed it,
-// kind 0 (full-length key) or 1 (the short tail key).
-struct Cand {
-  uint64_t p;
+// A gram position x found by the scan in (a chunk of) block k: a selected
+// gram that passed the bitmap filter, with its mixed hash mx; or, with the
+// top bit of x set, a position whose first gram hit the filter of keys
+// without an anchor.
+struct Hit {
+  uint64_t x;
   uint32_t k;
-  uint32_t kind;
+  uint32_t mx;
 };
+constexpr uint64_t kHitSec = 1ull << 63;
 
-// A full-length window at p (inside a run ending at av) matches slot sl.
+// A full-length window at p (inside a run ending at av) matches slot sl;
+// Hb = H[p + b].  Updates the slot minimum and joins the pair starting here.
 template <class M>
-__device__ __forceinline__ void on_block_hit(const ScanCtx<M>& C, uint32_t sl, uint64_t p,
-                                             uint64_t av) {
+__device__ __forceinline__ void on_block_hit(const ScanCtx<M>& C, uint32_t sl, uint64_t p, uint64_t av,
+                                             uint64_t Hb) {
   const Geo& g = C.g;
   min_pos(&C.blo[sl], p);
   if (p > C.maxpst[sl]) return;  // no pair starting with this slot can begin here or later
   if (p + 2 * g.b <= av) {
-    uint64_t fp2 = window_fast(C.m, g.T, g.Hs, g.PB, g.Bb, p + g.b, g.b);
-    uint32_t s2 = tbl_find(C.bkey, C.bmask, fp2);
+    const uint64_t fp2 = C.m.sub(g.H[p + 2 * g.b], C.m.mul(Hb, g.Bb));
+    const uint32_t s2 = tbl_find(C.bkey, C.bmask, fp2);
     if (s2 != kNoSlot) {
-      uint32_t ps = tbl_find(C.pkey, C.pmask, ((uint64_t)sl << 32) | s2);
+      const uint32_t ps = tbl_find(C.pkey, C.pmask, ((uint64_t)sl << 32) | s2);
       if (ps != kNoSlot) min_pos(&C.plo[ps], p);
     }
   }
   if (g.r && sl == C.pretail && p + g.b + g.r <= av &&
-      window_fast(C.m, g.T, g.Hs, g.PB, g.Br, p + g.b, g.r) == C.fp_tail)
+      window_fast(C.m, g.H, g.Br, p + g.b, g.r) == C.fp_tail)
     min_pos(&C.ld->lo_tailpair, p);
 }
 
@@ -444,57 +459,118 @@ __device__ __forceinline__ bool window_in_run(const Geo& g, uint64_t k, uint64_t
   return p + L <= *avp;
 }
 
-// Full-length candidate window at p: fingerprint -> block slot.
+// Test one candidate window.
 template <class M>
-__device__ __forceinline__ void try_block(const ScanCtx<M>& C, uint64_t k, uint64_t s, uint64_t av,
-                                          uint64_t p, uint32_t& ncand, uint32_t& nhit) {
-  uint64_t avp;
-  if (!window_in_run(C.g, k, s, av, p, C.g.b, &avp)) return;
+__device__ __forceinline__ void test_candidate(const ScanCtx<M>& C, uint64_t p, uint64_t avp, uint32_t kind,
+                                               uint32_t& ncand, uint32_t& nhit) {
+  const Geo& g = C.g;
+  if (kind) {
+    if (window_fast(C.m, g.H, g.Br, p, g.r) == C.fp_tail) min_pos(&C.ld->lo_tail, p);
+    return;
+  }
   ncand++;
-  const uint64_t fp = window_fast(C.m, C.g.T, C.g.Hs, C.g.PB, C.g.Bb, p, C.g.b);
+  const uint64_t Hb = g.H[p + g.b];
+  const uint64_t fp = C.m.sub(Hb, C.m.mul(g.H[p], g.Bb));
   const uint32_t sl = tbl_find(C.bkey, C.bmask, fp);
   if (sl != kNoSlot) {
     nhit++;
-    on_block_hit(C, sl, p, avp);
+    on_block_hit(C, sl, p, avp, Hb);
   }
 }
 
+// Test a proposed window that starts at p (kind 0: a full-length key, 1:
+// the short tail), if it lies inside a run.
 template <class M>
-__device__ __forceinline__ void try_tail(const ScanCtx<M>& C, uint64_t k, uint64_t s, uint64_t av,
-                                         uint64_t p) {
-  uint64_t avp;
-  if (!window_in_run(C.g, k, s, av, p, C.g.r, &avp)) return;
-  if (window_fast(C.m, C.g.T, C.g.Hs, C.g.PB, C.g.Br, p, C.g.r) == C.fp_tail)
-    min_pos(&C.ld->lo_tail, p);
-}
-
-// Queue a proposed window for k_candidates (one slot claim per group of
-// lanes that arrive together); when the queue is full, test it here.
-template <class M>
-__device__ __forceinline__ void propose(const ScanCtx<M>& C, uint64_t k, uint64_t s, uint64_t av,
-                                        uint64_t p, uint32_t kind, uint32_t& ncand, uint32_t& nhit) {
+__device__ __forceinline__ void propose(const ScanCtx<M>& C, uint64_t k, uint64_t s, uint64_t av, uint64_t p,
+                                        uint32_t kind, uint32_t& ncand, uint32_t& nhit) {
   uint64_t avp;
   if (!window_in_run(C.g, k, s, av, p, kind ? C.g.r : C.g.b, &avp)) return;
-  const unsigned active = __activemask();
-  const unsigned lane = threadIdx.x & 31;
-  const int leader = __ffs(active) - 1;
-  unsigned long long base = 0;
-  if ((int)lane == leader) base = atomicAdd(C.qn, (unsigned long long)__popc(active));
-  base = __shfl_sync(active, base, leader);
-  const unsigned long long idx = base + __popc(active & ((1u << lane) - 1u));
-  if (idx < C.qcap) {
-    C.q[idx] = Cand{p, (uint32_t)k, kind};
-  } else if (kind) {
-    try_tail(C, k, s, av, p);
-  } else {
-    try_block(C, k, s, av, p, ncand, nhit);
+  test_candidate(C, p, avp, kind, ncand, nhit);
+}
+
+// Record a hit in this CTA's segment (a shared-memory counter claims the
+// slot; past the segment's end only the count grows).
+template <class M>
+__device__ __forceinline__ void record_hit(const ScanCtx<M>& C, unsigned int* sq, uint64_t x, uint64_t k,
+                                           uint32_t mx) {
+  const uint32_t idx = atomicAdd(sq, 1u);
+  if (idx < C.seg) C.q[blockIdx.x * (uint64_t)C.seg + idx] = Hit{x, (uint32_t)k, mx};
+}
+
+// The anchor-table lookup of a hit at x (mixed gram mx) in block k and the
+// test of every window its anchors propose.
+template <class M>
+__device__ __forceinline__ void anchor_hit(const ScanCtx<M>& C, const AnchorSet* __restrict__ atab,
+                                           uint32_t amask, uint32_t tail_gram, uint32_t tail_a, uint64_t k,
+                                           uint64_t s, uint64_t av, uint64_t x, uint32_t mx, uint32_t& ncand,
+                                           uint32_t& nhit) {
+  const uint32_t gk = gram_key(mx);
+  unsigned long long offs = 0, maxst = 0;
+  uint32_t far = kNoFar;
+  for (uint32_t h = gram_slot(gk, amask), it = 0; it <= amask; h = (h + 1) & amask, it++) {
+    const uint32_t eg = atab[h].gram;
+    if (eg == gk) {
+      offs = atab[h].offs;
+      far = atab[h].far;
+      maxst = atab[h].maxst;
+      break;
+    }
+    if (eg == kEmptyGram) break;
+  }
+  // A window that starts after every key anchored on this gram cannot be
+  // the leftmost occurrence of any of them, nor of a pair that starts with
+  // one of them (both are at or before the key's start).
+  bool pt = gk == tail_gram && x >= tail_a;
+  bool pf = far != kNoFar && far <= x && x - far <= maxst;
+  while (offs || pf || pt) {
+    uint64_t p = 0;
+    uint32_t kind = 0;
+    bool ok = true;
+    if (pt) {
+      pt = false;
+      p = x - tail_a;
+      kind = 1;
+    } else if (offs) {
+      const uint32_t a = __ffsll(offs) - 1;
+      offs &= offs - 1;
+      ok = a <= x && x - a <= maxst;
+      p = x - a;
+    } else {
+      pf = false;
+      p = x - far;
+    }
+    if (ok) propose(C, k, s, av, p, kind, ncand, nhit);
   }
 }
 
-// Copy T[a, a+cnt) into a thread's shared-memory slot: 16-byte loads for the
-// aligned body when the text is 16-byte aligned, bytes for the rest.
+// Copy T[a, a+cnt) (cnt <= 144) into a thread's shared-memory slot.  When a
+// is 16-byte aligned (block starts are multiples of 16 at the usual leaf
+// lengths) the whole 16-byte units covering it are loaded at once, all in
+// flight together; otherwise 16-byte loads for the aligned body and bytes
+// for the rest.
 __device__ __forceinline__ void stage(uint8_t* slot, const uint8_t* __restrict__ T, uint64_t n,
                                       uint64_t a, uint32_t cnt, bool aligned16) {
+  const uint32_t units = (cnt + 15) / 16;
+  if (aligned16 && (a & 15) == 0 && a + 16ull * units <= n) {
+    const uint4* src = (const uint4*)(T + a);
+    uint32_t* d = (uint32_t*)slot;
+#pragma unroll
+    for (uint32_t h = 0; h < 9; h += 5) {  // two batches of loads in flight
+      uint4 v[5];
+#pragma unroll
+      for (uint32_t u = 0; u < 5; u++)
+        if (h + u < units) v[u] = src[h + u];
+#pragma unroll
+      for (uint32_t u = 0; u < 5; u++)
+        if (h + u < units) {
+          d[4 * (h + u)] = v[u].x;
+          d[4 * (h + u) + 1] = v[u].y;
+          d[4 * (h + u) + 2] = v[u].z;
+          d[4 * (h + u) + 3] = v[u].w;
+        }
+    }
+    return;
+  }
   uint32_t i = 0;
   if (aligned16) {
     const uint64_t a16 = (a + 15) & ~15ull;
@@ -518,18 +594,46 @@ __device__ __forceinline__ void stage(uint8_t* slot, const uint8_t* __restrict__
   for (; i < cnt; i++) slot[i] = T[a + i];
 }
 
-template <class M>
+// Mixed gram hash at slot position i, from the staged bytes.
+__device__ __forceinline__ uint32_t gram_at(const uint8_t* slot, uint32_t i, uint32_t w, uint32_t rb) {
+  uint32_t h = 0;
+  for (uint32_t t = 0; t < w; t++) h = h * rb + slot[i + t];
+  return gram_mix(h);
+}
+
+__device__ __forceinline__ uint32_t pick4(uint32_t G, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  return G == 0 ? a : G == 1 ? b : G == 2 ? c : d;
+}
+
+// Record a position's mixed gram: selected ones set bit BIT of V and enter
+// the ring at rp (the ring pointer advances and saturates at rlim; entries
+// past kRing - 1 are recomputed when needed).
+#define BT_RECORD(MX, V, BIT)                      \
+  {                                                \
+    const bool sel_ = (MX) <= sel_max;             \
+    *rp = (MX);                                    \
+    rp += sel_ ? kScanThreads : 0u;                \
+    rp = rp < rlim ? rp : rlim;                    \
+    if (sel_) V |= 1u << (BIT);                    \
+  }
+
+// INLINE = false: the scan, which queues proposed windows.  INLINE = true:
+// runs only when the queue overflowed, and tests every proposed window here.
+template <class M, bool INLINE>
 __global__ void __launch_bounds__(kScanThreads, 3) k_scan_anchor(ScanCtx<M> C0, GramP gp, uint64_t cpb,
                                                              const AnchorSet* __restrict__ atab,
                                                              uint32_t amask,
                                                              const uint32_t* __restrict__ bitmap_g,
                                                              uint32_t bm_smem_words,
                                                              const uint32_t* __restrict__ secbits_g) {
+  if (INLINE && C0.ld->qover == 0) return;
   extern __shared__ uint32_t smem[];
-  uint32_t* sec = smem;                               // kSecBits / 32 words
-  uint32_t* bms = smem + kSecBits / 32;               // bm_smem_words words
-  uint8_t* slots = (uint8_t*)(bms + bm_smem_words);
-  uint8_t* slot = slots + threadIdx.x * kSlotBytes;
+  __shared__ unsigned int s_qn;  // hits this CTA recorded
+  uint32_t* sec = smem;                                      // kSecBits / 32 words
+  uint32_t* ring = sec + kSecBits / 32 + threadIdx.x;        // kRing x kScanThreads, this thread's column
+  uint32_t* bms = smem + kSecBits / 32 + kRing * kScanThreads;  // bm_smem_words words
+  uint32_t* slotw = bms + bm_smem_words + threadIdx.x * kSlotWords;
+  uint8_t* slot = (uint8_t*)slotw;
   ScanCtx<M> C = C0;
   C.pretail = C.ld->pretail_slot;
   C.fp_tail = C.ld->fp_tail;
@@ -537,120 +641,248 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_anchor(ScanCtx<M> C0, 
   const bool anchorless = C.ld->anchorless == 1u;
   const bool tail_sec = C.ld->tail_anchorless == 2u;
   const uint32_t tail_gram = C.ld->tail_gram, tail_a = C.ld->tail_a;
+  // Anchors lie below a window's start + Wx (+ Wt for the tail window).
+  const uint32_t far_end = C.ld->far_end;
+  const uint32_t Wx = gp.W > far_end ? gp.W : far_end;
+  const uint32_t Wt0 = gp.Wr ? gp.Wr : 1;
+  const uint32_t Wt = tail_a != 0xFFFFFFFFu && tail_a + 1 > Wt0 ? tail_a + 1 : Wt0;
   for (uint32_t i = threadIdx.x; i < kSecBits / 32; i += blockDim.x) sec[i] = secbits_g[i];
   for (uint32_t i = threadIdx.x; i < bm_smem_words; i += blockDim.x) bms[i] = bitmap_g[i];
+  if (threadIdx.x == 0) s_qn = 0;
   __syncthreads();
   const uint32_t* bitmap = bm_smem_words ? bms : bitmap_g;
   const bool check_sec = anchorless || tail_sec;
   const bool aligned16 = (((uintptr_t)g.T) & 15) == 0;
-  const uint32_t w = gp.w, rb = gp.rb, rw = gp.rw, sbits = gp.sbits, fbits = gp.fbits;
+  const uint32_t w = gp.w, rb = gp.rb, rw = gp.rw, sel_max = gp.sel_max;
+  uint32_t* const rlim = ring + (kRing - 1) * kScanThreads;
   const uint64_t total = g.c * cpb;
   uint32_t ncand = 0, nhit = 0;
-  for (uint64_t wi = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; wi < total;
-       wi += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t k = wi / cpb, j = wi - k * cpb;
-    const uint64_t s = g.st[k], len = blen(g, k);
-    const uint64_t p0 = s + j * kAnchorQ;
-    if (p0 >= s + len) continue;
-    const uint64_t av = avail_end(g, k);
-    // Gram positions x in [p0, xe): owned by this thread and able to anchor a
-    // window that fits in the run (anchors of a length-L window lie below
-    // its start + W_L; windows without anchors start at their first gram).
-    uint64_t xe = p0 + kAnchorQ < s + len ? p0 + kAnchorQ : s + len;
-    uint64_t xm = av >= g.b ? av - g.b + gp.W : 0;
-    if (g.r && av >= g.r) {
-      const uint64_t xr = av - g.r + (gp.Wr ? gp.Wr : 1);
-      if (xr > xm) xm = xr;
-    }
-    const uint64_t gram_end = av + 1 >= w ? av + 1 - w : 0;  // grams must fit in the run
-    if (xm > gram_end) xm = gram_end;
-    if (xe > xm) xe = xm;
-    if (xe <= p0) continue;
-    const uint32_t nx = (uint32_t)(xe - p0);
-    stage(slot, g.T, g.n, p0, nx + w - 1, aligned16);
-    // Pass 1: roll the gram hash; mark positions whose gram is selected and
-    // passes the bitmap filter (m0/m1), or hits the first-gram filter of keys
-    // without an anchor (q0/q1).
-    unsigned long long m0 = 0, m1 = 0, q0 = 0, q1 = 0;
-    uint32_t gh = 0;
-    for (uint32_t i = 0; i < w; i++) gh = gh * rb + slot[i];
-    for (uint32_t i = 0; i < nx; i++) {
-      if (i) gh = gh * rb - (uint32_t)slot[i - 1] * rw + slot[i + w - 1];
-      if (check_sec) {
-        const uint32_t sb = sec_bit(gh);
-        if ((sec[sb >> 5] >> (sb & 31)) & 1u) {
-          if (i < 64) q0 |= 1ull << i;
-          else q1 |= 1ull << (i - 64);
-        }
+  // Warp-uniform trip count and a single-exit body, so that the lanes of a
+  // warp meet again after every chunk.
+  const unsigned lane = threadIdx.x & 31;
+  for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x + (threadIdx.x & ~31u); base < total;
+       base += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t wi = base + lane;
+    do {
+      if (wi >= total) break;
+      const uint64_t k = cpb == 1 ? wi : wi / cpb, j = wi - k * cpb;
+      const uint64_t s = g.st[k], len = blen(g, k);
+      const uint64_t p0 = s + j * kAnchorQ;
+      if (p0 >= s + len) break;
+      const uint64_t av = avail_end(g, k);
+      // Gram positions x in [p0, xe): owned by this thread and able to anchor a
+      // window that fits in the run (windows without an anchor start at their
+      // first gram).
+      uint64_t xe = p0 + kAnchorQ < s + len ? p0 + kAnchorQ : s + len;
+      uint64_t xm = av >= g.b ? av - g.b + Wx : 0;
+      if (g.r && av >= g.r) {
+        const uint64_t xr = av - g.r + Wt;
+        if (xr > xm) xm = xr;
       }
-      const uint32_t mix = gh * kFibMul;
-      if (sbits && (mix >> (32 - sbits))) continue;
-      const uint32_t bit = (mix << sbits) >> (32 - fbits);
-      if (!((bitmap[bit >> 5] >> (bit & 31)) & 1u)) continue;
-      if (i < 64) m0 |= 1ull << i;
-      else m1 |= 1ull << (i - 64);
-    }
-    // Pass 2: the marked positions (rare).
-    for (int half = 0; half < 2; half++) {
-      unsigned long long mm = half ? m1 : m0, qq = half ? q1 : q0;
-      while (mm | qq) {
-        const uint32_t bi = __ffsll(mm | qq) - 1;
-        const unsigned long long one = 1ull << bi;
-        const bool is_anchor = mm & one, is_sec = qq & one;
-        mm &= ~one;
-        qq &= ~one;
-        const uint32_t i = bi + 64u * half;
-        const uint64_t x = p0 + i;
-        uint32_t gx = 0;
-        for (uint32_t t = 0; t < w; t++) gx = gx * rb + slot[i + t];
-        if (is_sec) {
-          if (anchorless) propose(C, k, s, av, x, 0, ncand, nhit);
-          if (tail_sec) propose(C, k, s, av, x, 1, ncand, nhit);
+      const uint64_t gram_end = av + 1 >= w ? av + 1 - w : 0;  // grams must fit in the run
+      if (xm > gram_end) xm = gram_end;
+      if (xe > xm) xe = xm;
+      if (xe <= p0) break;
+      const uint32_t nx = (uint32_t)(xe - p0);
+      if (p0 + nx + w - 1 > g.n || av > g.n) {  // invariant: grams lie inside the text
+        atomicExch(&C.status->error, 8ull);
+        break;
+      }
+      stage(slot, g.T, g.n, p0, nx + w - 1, aligned16);
+      // Pass 1: roll the gram hash; selected grams set a bit of (m0, m1, m2, m3)
+      // (positions 0-31, 32-63, ...) and enter the ring.  Positions past nx
+      // are masked off afterwards (their ring entries follow the valid ones).
+      uint32_t m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+      uint32_t* rp = ring;
+      if (w == 16) {
+        // The transition to position i removes byte i-1 and adds byte i+15, so
+        // positions 4q+1 .. 4q+4 take the bytes of words q and q+4.
+        uint32_t gh = 0;
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+          const uint32_t v = slotw[t];
+#pragma unroll
+          for (int u = 0; u < 4; u++) gh = gh * rb + __byte_perm(v, 0, 0x4440 + u);
         }
-        if (!is_anchor) continue;
-        const uint32_t gk = gram_key(gx);
-        if (gk == tail_gram && x >= tail_a) propose(C, k, s, av, x - tail_a, 1, ncand, nhit);
-        unsigned long long offs = 0, maxst = 0;
-        for (uint32_t h = gram_slot(gk, amask), it = 0; it <= amask; h = (h + 1) & amask, it++) {
-          const uint32_t eg = atab[h].gram;
-          if (eg == gk) {
-            offs = atab[h].offs;
-            maxst = atab[h].maxst;
-            break;
+        uint32_t cur = 0;
+        {
+          const uint32_t mx = gram_mix(gh);
+          BT_RECORD(mx, cur, 0);
+        }
+        const uint32_t ngroups = (nx + 31) / 32;
+#pragma unroll 1
+        for (uint32_t G = 0; G < 4; G++) {
+          uint32_t carry = 0;
+          if (G < ngroups) {
+#pragma unroll
+            for (uint32_t qq = 0; qq < 8; qq++) {
+              const uint32_t wo = slotw[8 * G + qq], wn = slotw[8 * G + qq + 4];
+#pragma unroll
+              for (uint32_t u = 0; u < 4; u++) {
+                gh = gh * rb + __byte_perm(wn, 0, 0x4440 + u) - __byte_perm(wo, 0, 0x4440 + u) * rw;
+                const uint32_t mx = gram_mix(gh);
+                if (4 * qq + u + 1 < 32) {
+                  BT_RECORD(mx, cur, (4 * qq + u + 1) & 31);
+                } else {
+                  BT_RECORD(mx, carry, 0);
+                }
+              }
+            }
           }
-          if (eg == kEmptyGram) break;
+          m3 = m2;
+          m2 = m1;
+          m1 = m0;
+          m0 = cur;
+          cur = carry;
         }
-        // A window that starts after every key anchored on this gram cannot
-        // be the leftmost occurrence of any of them, nor of a pair that
-        // starts with one of them (both are at or before the key's start).
-        while (offs) {
-          const uint32_t a = __ffsll(offs) - 1;
-          offs &= offs - 1;
-          if (a <= x && x - a <= maxst) propose(C, k, s, av, x - a, 0, ncand, nhit);
+        // After four shifts m3 holds positions 0-31, ..., m0 positions 96-127.
+        const uint32_t t0 = m3, t1 = m2;
+        m3 = m0;
+        m2 = m1;
+        m0 = t0;
+        m1 = t1;
+      } else {
+        uint32_t gh = 0;
+        for (uint32_t i = 0; i < w; i++) gh = gh * rb + slot[i];
+        for (uint32_t i = 0; i < nx; i++) {
+          if (i) gh = gh * rb - (uint32_t)slot[i - 1] * rw + slot[i + w - 1];
+          const uint32_t mx = gram_mix(gh);
+          uint32_t bv = 0;
+          BT_RECORD(mx, bv, 0);
+          const uint32_t sh = bv << (i & 31);
+          if (i < 32) m0 |= sh;
+          else if (i < 64) m1 |= sh;
+          else if (i < 96) m2 |= sh;
+          else m3 |= sh;
         }
       }
-    }
+      // Keep positions below nx.
+      if (nx < 128) {
+        m3 &= nx > 96 ? 0xFFFFFFFFu >> (128 - nx) : 0u;
+        m2 &= nx >= 96 ? 0xFFFFFFFFu : nx > 64 ? 0xFFFFFFFFu >> (96 - nx) : 0u;
+        m1 &= nx >= 64 ? 0xFFFFFFFFu : nx > 32 ? 0xFFFFFFFFu >> (64 - nx) : 0u;
+        m0 &= nx >= 32 ? 0xFFFFFFFFu : 0xFFFFFFFFu >> (32 - nx);
+      }
+      const uint32_t c0 = __popc(m0), c1 = __popc(m1), c2 = __popc(m2);
+      const uint32_t nsel = c0 + c1 + c2 + __popc(m3);
+      const uint32_t exact = nsel < kRing ? nsel : kRing - 1;  // ring entries [0, exact) hold their gram
+      // Pass 2a: bitmap filter of the selected grams, four loads in flight.
+      uint32_t h0 = 0, h1 = 0, h2 = 0, h3 = 0;
+      {
+        uint32_t jr = 0;
+#pragma unroll 1
+        for (uint32_t G = 0; G < 4; G++) {
+          uint32_t mm = pick4(G, m0, m1, m2, m3);
+          uint32_t hit = 0;
+          while (mm) {
+            uint32_t pos[4], wv[4], bt[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+              pos[u] = 32;
+              wv[u] = 0;
+              bt[u] = 0;
+              if (mm) {
+                const uint32_t bpos = __ffs(mm) - 1;
+                mm &= mm - 1;
+                const uint32_t mx = jr < exact ? ring[jr * kScanThreads] : gram_at(slot, 32 * G + bpos, w, rb);
+                jr++;
+                const uint32_t bit = gram_bit(gp, mx);
+                pos[u] = bpos;
+                bt[u] = bit & 31;
+                wv[u] = bitmap[bit >> 5];
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+              if (pos[u] < 32 && ((wv[u] >> bt[u]) & 1u)) hit |= 1u << pos[u];
+          }
+          if (G == 0) h0 = hit;
+          else if (G == 1) h1 = hit;
+          else if (G == 2) h2 = hit;
+          else h3 = hit;
+        }
+      }
+      // Pass 2b: the grams that passed the filter go to k_hits (INLINE: their
+      // anchor-table lookup and window tests happen here).
+#pragma unroll 1
+      for (uint32_t G = 0; G < 4; G++) {
+        uint32_t hm = pick4(G, h0, h1, h2, h3);
+        const uint32_t below = pick4(G, 0, c0, c0 + c1, c0 + c1 + c2);
+        const uint32_t mg = pick4(G, m0, m1, m2, m3);
+        while (hm) {
+          const uint32_t bpos = __ffs(hm) - 1;
+          hm &= hm - 1;
+          const uint32_t i = 32 * G + bpos;
+          const uint32_t jr = below + __popc(mg & ((1u << bpos) - 1u));
+          const uint32_t mx = jr < exact ? ring[jr * kScanThreads] : gram_at(slot, i, w, rb);
+          if (INLINE) anchor_hit(C, atab, amask, tail_gram, tail_a, k, s, av, p0 + i, mx, ncand, nhit);
+          else record_hit(C, &s_qn, p0 + i, k, mx);
+        }
+      }
+      // Pass 2c: windows of keys without an anchor start at a gram in the
+      // first-gram filter (only when such keys exist).
+      if (check_sec) {
+        uint32_t gh = 0;
+        for (uint32_t i = 0; i < w; i++) gh = gh * rb + slot[i];
+        for (uint32_t i = 0; i < nx; i++) {
+          if (i) gh = gh * rb - (uint32_t)slot[i - 1] * rw + slot[i + w - 1];
+          const uint32_t sb = sec_bit(gram_mix(gh));
+          if ((sec[sb >> 5] >> (sb & 31)) & 1u) {
+            if (!INLINE) {
+              record_hit(C, &s_qn, (p0 + i) | kHitSec, k, 0);
+            } else {
+#pragma unroll 1
+              for (uint32_t kind = 0; kind < 2; kind++)
+                if (kind ? tail_sec : anchorless) propose(C, k, s, av, p0 + i, kind, ncand, nhit);
+            }
+          }
+        }
+      }
+    } while (0);
   }
   if (ncand) atomicAdd(&C.ld->cands, (unsigned long long)ncand);
   if (nhit) atomicAdd(&C.ld->hits, (unsigned long long)nhit);
+  if (!INLINE) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      C.segn[blockIdx.x] = s_qn;
+      atomicAdd(C.qn, (unsigned long long)s_qn);
+      if (s_qn > C.seg) C.ld->qover = 1u;
+    }
+  }
 }
+#undef BT_RECORD
 
-// Test the queued candidate windows: one per thread.
+// The hits of scan CTA j's segment, one per thread: anchor-table lookup and
+// the test of every proposed window.
 template <class M>
-__global__ void __launch_bounds__(256) k_candidates(ScanCtx<M> C0) {
+__global__ void __launch_bounds__(512) k_hits(ScanCtx<M> C0, const AnchorSet* __restrict__ atab,
+                                              uint32_t amask) {
   ScanCtx<M> C = C0;
   C.pretail = C.ld->pretail_slot;
   C.fp_tail = C.ld->fp_tail;
-  const unsigned long long qn = *C.qn;
-  const uint64_t n = qn < C.qcap ? qn : C.qcap;
+  const Geo& g = C.g;
+  const bool anchorless = C.ld->anchorless == 1u;
+  const bool tail_sec = C.ld->tail_anchorless == 2u;
+  const uint32_t tail_gram = C.ld->tail_gram, tail_a = C.ld->tail_a;
+  const uint32_t sn = C.segn[blockIdx.x];
+  const uint32_t n = sn < C.seg ? sn : C.seg;
+  const Hit* q = C.q + blockIdx.x * (uint64_t)C.seg;
   uint32_t ncand = 0, nhit = 0;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    const Cand e = C.q[i];
-    const uint64_t s = C.g.st[e.k];
-    const uint64_t av = avail_end(C.g, e.k);
-    if (e.kind) try_tail(C, e.k, s, av, e.p);
-    else try_block(C, e.k, s, av, e.p, ncand, nhit);
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const Hit e = q[i];
+    const uint64_t x = e.x & ~kHitSec;
+    if (e.k >= g.c || x >= g.n) {  // invariant check
+      atomicExch(&C.status->error, 9ull);
+      continue;
+    }
+    const uint64_t k = e.k, s = g.st[k], av = avail_end(g, k);
+    if (e.x & kHitSec) {
+      if (anchorless) propose(C, k, s, av, x, 0, ncand, nhit);
+      if (tail_sec) propose(C, k, s, av, x, 1, ncand, nhit);
+    } else {
+      anchor_hit(C, atab, amask, tail_gram, tail_a, k, s, av, x, e.mx, ncand, nhit);
+    }
   }
   if (ncand) atomicAdd(&C.ld->cands, (unsigned long long)ncand);
   if (nhit) atomicAdd(&C.ld->hits, (unsigned long long)nhit);
@@ -765,7 +997,7 @@ __global__ void __launch_bounds__(256) k_exact_scan(M m, Geo g, uint64_t cpb, in
     const uint64_t pend = (p0 + kScanQ < s + len) ? p0 + kScanQ : s + len;
     const uint64_t av = avail_end(g, k);
     if (p0 + klen > av) continue;
-    uint64_t fp = window_fast(m, g.T, g.Hs, g.PB, BL, p0, klen);
+    uint64_t fp = window_fast(m, g.H, BL, p0, klen);
     for (uint64_t p = p0; p < pend && p < ks && p + klen <= av; p++) {
       if (p > p0) {
         uint64_t out = (uint64_t)g.T[p - 1] + 1, in = (uint64_t)g.T[p + klen - 1] + 1;
@@ -994,6 +1226,7 @@ __global__ void k_level_init(InitArgs a) {
     if (i < a.c) a.mismatch[i] = 0;
     if (a.atab && i < a.acap) {
       a.atab[i].gram = kEmptyGram;
+      a.atab[i].far = kNoFar;
       a.atab[i].offs = 0;
       a.atab[i].maxst = 0;
     }
@@ -1012,6 +1245,8 @@ __global__ void k_level_init(InitArgs a) {
       d.tail_anchorless = 0;
       d.tail_gram = 0xFFFFFFFFu;
       d.tail_a = 0xFFFFFFFFu;
+      d.far_end = 0;
+      d.qover = 0;
       d.cands = 0;
       d.hits = 0;
       *a.ld = d;
@@ -1036,14 +1271,26 @@ __global__ void k_reset_jobs(unsigned int* mismatch, uint64_t c, LevelDev* ld) {
 // even over small or skewed alphabets, so few keys share an anchor gram;
 // anchor range W <= 64; selection density 2^-sbits chosen so that
 // W / 2^sbits >= 8 (a window without an anchor is then rare).
-GramP choose_gram(uint64_t b, uint64_t r, uint32_t S) {
-  (void)S;
+// Gram length w = 16 (half the block when shorter), near range W <= 64.
+// Each gram is selected with probability 2^-sbits, so a key has no selected
+// gram among its first npos positions with probability (1 - 2^-sbits)^npos;
+// sbits is the largest value in 0..3 that leaves well under one such key per
+// level (c keys), since those keys are found by a per-position filter.
+GramP choose_gram(uint64_t b, uint64_t r, uint64_t c) {
   uint32_t w = 16;
   if (w > b / 2) w = (uint32_t)(b / 2 > 0 ? b / 2 : 1);
   GramP gp;
   gp.w = w;
   gp.W = (uint32_t)(b - w + 1 < kAnchorWmax ? b - w + 1 : kAnchorWmax);
-  gp.sbits = gp.W >= 64 ? 3 : gp.W >= 32 ? 2 : gp.W >= 16 ? 1 : 0;
+  const double npos = (double)(b - w + 1 < kFarMax ? b - w + 1 : kFarMax);
+  gp.sbits = 0;
+  for (uint32_t sb = 3; sb >= 1; sb--) {
+    if ((double)c * std::pow(1.0 - std::ldexp(1.0, -(int)sb), npos) <= 0.02) {
+      gp.sbits = sb;
+      break;
+    }
+  }
+  gp.sel_max = gp.sbits ? (1u << (32 - gp.sbits)) - 1u : 0xFFFFFFFFu;
   gp.Wr = (r && r >= w) ? (uint32_t)(r - w + 1 < kAnchorWmax ? r - w + 1 : kAnchorWmax) : 0;
   gp.fbits = 12;
   gp.rb = 0x01000193u;
@@ -1051,6 +1298,45 @@ GramP choose_gram(uint64_t b, uint64_t r, uint32_t S) {
   for (uint32_t i = 0; i < w; i++) rw *= gp.rb;
   gp.rw = rw;
   return gp;
+}
+
+// Streaming multiprocessors of the current device (cached per device).
+unsigned sm_count() {
+  static std::atomic<unsigned> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  unsigned v = cache[dev].load(std::memory_order_relaxed);
+  if (v) return v;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+  cache[dev].store((unsigned)n, std::memory_order_relaxed);
+  return (unsigned)n;
+}
+
+// CTAs of a kernel that fit on one SM at once (at least 1).
+template <class F>
+unsigned resident_ctas(F* fn, int threads, size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    n = 1;
+  }
+  return (unsigned)n;
+}
+
+// Opt a kernel in to more than 48 KiB of dynamic shared memory, once per
+// device (the attribute is a property of the function on each device; the
+// template parameter gives every kernel its own flags).
+template <auto FN>
+int allow_scan_smem(int bytes) {
+  static std::atomic<uint64_t> done{0};
+  int dev = 0;
+  BT_CUDA(cudaGetDevice(&dev));
+  const uint64_t bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return BT_OK;
+  BT_CUDA(cudaFuncSetAttribute(FN, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.fetch_or(bit, std::memory_order_acq_rel);
+  return BT_OK;
 }
 
 uint64_t pow2_at_least(uint64_t x) {
@@ -1093,8 +1379,7 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
   Geo g;
   g.T = ctx.T;
   g.n = n;
-  g.Hs = ctx.Hs;
-  g.PB = ctx.PB;
+  g.H = ctx.H;
   g.B = t->B;
   g.Bb = pow_mod(m, t->B, b);
   g.Br = r ? pow_mod(m, t->B, r) : 0;
@@ -1110,7 +1395,7 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
   const unsigned gc = grid_for(c, T);
   const uint64_t words = (c + 31) / 32;
   const bool anchored = !ctx.dense_scan;
-  const GramP gp = choose_gram(b, r, t->S);
+  const GramP gp = choose_gram(b, r, c);
   const uint64_t acap = anchored ? pow2_at_least(2 * (c + 2)) : 0;
   GramP gq = gp;
   uint64_t bwords = 0;
@@ -1123,18 +1408,26 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
     gq.fbits = fbits;
     bwords = (1ull << fbits) / 32;
   }
-  // Candidate queue: a few candidates per covered window is plenty; more
-  // are tested inline by the scan.
+  // Anchored scan launch: one wave of resident CTAs (shared memory allows 3
+  // per SM, 2 with the bitmap in shared memory); threads stride over chunks.
+  const uint64_t cpa = (b + kAnchorQ - 1) / kAnchorQ;
+  const uint32_t bm_smem = bwords <= kSmemBitmapWords ? (uint32_t)bwords : 0;
+  const unsigned scan_grid = anchored ? grid_for(c * cpa, kScanThreads, sm_count() * (bm_smem ? 2u : 3u)) : 0;
+  // Hit queue, one segment per scan CTA: a few hits per covered window is
+  // plenty; if a segment overflows, a second scan tests windows in place.
   const uint64_t cov_l = (c - 1) * b + (len_last < b ? len_last : b);
   uint64_t qcap = cov_l / 2 + 4096;
   if (qcap > (64ull << 20)) qcap = 64ull << 20;
+  if (ctx.tiny_queue) qcap = 64;
+  const uint32_t seg = anchored ? (uint32_t)(qcap / scan_grid) : 0;
 
   // Scratch: carved from the build's arena (a dry carving sizes it).
   Arena& A = ctx.arena;
   LevelWork W;
   AnchorSet* atab = nullptr;
   uint32_t *bitmap = nullptr, *secbits = nullptr, *sagg = nullptr;
-  Cand* q = nullptr;
+  Hit* q = nullptr;
+  uint32_t* segn = nullptr;
   unsigned long long* qn = nullptr;
   auto carve = [&]() {
     W.fpB = A.take<uint64_t>(c);
@@ -1160,7 +1453,8 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
       atab = A.take<AnchorSet>(acap);
       bitmap = A.take<uint32_t>(bwords);
       secbits = A.take<uint32_t>(kSecBits / 32);
-      q = A.take<Cand>(qcap);
+      q = A.take<Hit>((uint64_t)seg * scan_grid);
+      segn = A.take<uint32_t>(scan_grid);
       qn = A.take<unsigned long long>(1);
     }
   };
@@ -1201,21 +1495,22 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
   } else {
     BT_LAUNCH(k_anchor_keys<<<gc, T, 0, s>>>(g, gq, W.slotB, atab, (uint32_t)(acap - 1), bitmap, secbits,
                                              W.ld, ctx.st));
-    ScanCtx<M> C{m, g, W.bkey, bcap - 1, W.blo, W.pkey, pcap - 1, W.plo, W.ld, 0, 0, W.maxpst, q, qn, qcap};
-    const uint64_t cpa = (b + kAnchorQ - 1) / kAnchorQ;
-    const uint32_t bm_smem = bwords <= kSmemBitmapWords ? (uint32_t)bwords : 0;
-    const size_t smem = (kSecBits / 32 + bm_smem) * 4 + (size_t)kScanThreads * kSlotBytes;
-    static bool attr_set = false;
-    if (!attr_set) {
-      BT_CUDA(cudaFuncSetAttribute(k_scan_anchor<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(((size_t)kSecBits / 32 + kSmemBitmapWords) * 4 +
-                                         (size_t)kScanThreads * kSlotBytes)));
-      attr_set = true;
-    }
+    ScanCtx<M> C{m, g, W.bkey, bcap - 1, W.blo, W.pkey, pcap - 1, W.plo, W.ld, 0, 0, W.maxpst,
+                 q, segn, seg, qn, ctx.st};
+    const size_t smem_base = ((size_t)kSecBits / 32 + (size_t)kRing * kScanThreads +
+                              (size_t)kScanThreads * kSlotWords) * 4;
+    const size_t smem = smem_base + (size_t)bm_smem * 4;
+    const int smem_max = (int)(smem_base + (size_t)kSmemBitmapWords * 4);
+    int rc_a = allow_scan_smem<k_scan_anchor<M, false>>(smem_max);
+    if (rc_a == BT_OK) rc_a = allow_scan_smem<k_scan_anchor<M, true>>(smem_max);
+    if (rc_a != BT_OK) return rc_a;
     ProfScope ps("window_scan", s, cov_l);
-    BT_LAUNCH(k_scan_anchor<M><<<grid_for(c * cpa, kScanThreads, 152 * 8), kScanThreads, smem, s>>>(
+    BT_LAUNCH(k_scan_anchor<M, false><<<scan_grid, kScanThreads, smem, s>>>(
         C, gq, cpa, atab, (uint32_t)(acap - 1), bitmap, bm_smem, secbits));
-    BT_LAUNCH(k_candidates<M><<<152 * 16, 256, 0, s>>>(C));
+    BT_LAUNCH(k_hits<M><<<scan_grid, 512, 0, s>>>(C, atab, (uint32_t)(acap - 1)));
+    // Only when the queue overflowed: the scan again, testing windows inline.
+    BT_LAUNCH(k_scan_anchor<M, true><<<scan_grid, kScanThreads, smem, s>>>(
+        C, gq, cpa, atab, (uint32_t)(acap - 1), bitmap, bm_smem, secbits));
     if (r)
       BT_LAUNCH(k_scan<M><<<grid_for(c * cpb, T), T, 0, s>>>(m, g, cpb, W.bkey, bcap - 1, W.blo, W.pkey,
                                                               pcap - 1, W.plo, W.ld, 1));

@@ -223,6 +223,50 @@ int kr_prefix(const M& m, const uint8_t* T, uint64_t n, uint64_t B, uint64_t* Hs
   return BT_OK;
 }
 
+// H[p] at every position from the stride-32 values: the lane of chunk j
+// extends Hs[j] by Horner over the chunk's bytes (section 2), keeping the 32
+// prefixes in a shared-memory tile; the warp then writes the tile row by row
+// so that each store covers 32 consecutive positions.
+constexpr uint32_t kExpandWarps = 4;
+
+template <class M>
+__global__ void __launch_bounds__(32 * kExpandWarps) k_kr_expand(M m, const uint8_t* __restrict__ T,
+                                                                uint64_t n, uint64_t B,
+                                                                const uint64_t* __restrict__ Hs,
+                                                                uint64_t* __restrict__ H) {
+  __shared__ uint64_t tile[kExpandWarps][32][33];
+  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t nchunks = n / kPrefixStride + 1;  // the last one may be partial
+  const uint64_t j0 = ((uint64_t)blockIdx.x * kExpandWarps + warp) * 32;
+  const uint64_t j = j0 + lane;
+  if (j < nchunks) {
+    uint64_t h = Hs[j];
+    const uint64_t p0 = j * kPrefixStride;
+#pragma unroll 4
+    for (uint32_t i = 0; i < kPrefixStride; i++) {
+      tile[warp][lane][i] = h;
+      if (p0 + i < n) h = m.add(m.mul(h, B), (uint64_t)T[p0 + i] + 1);
+    }
+  }
+  __syncwarp();
+  for (uint32_t r = 0; r < 32 && j0 + r < nchunks; r++) {
+    const uint64_t p = (j0 + r) * kPrefixStride + lane;
+    if (p <= n) H[p] = tile[warp][r][lane];
+  }
+}
+
+template <class M>
+int kr_expand(const M& m, const uint8_t* T, uint64_t n, uint64_t B, const uint64_t* Hs, uint64_t* H,
+              cudaStream_t s) {
+  const uint64_t nchunks = n / kPrefixStride + 1;
+  const uint64_t per_cta = 32ull * kExpandWarps;
+  ProfScope ps("prefix_expand", s, n);
+  BT_LAUNCH(k_kr_expand<M><<<(unsigned)((nchunks + per_cta - 1) / per_cta), 32 * kExpandWarps, 0, s>>>(
+      m, T, n, B, Hs, H));
+  BT_CUDA(cudaGetLastError());
+  return BT_OK;
+}
+
 }  // namespace
 
 int scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, cudaStream_t s) {
@@ -248,6 +292,12 @@ int prefix_fingerprints(const uint8_t* T, uint64_t n, uint64_t B, uint64_t q, ui
                         cudaStream_t s) {
   if (q == Mersenne61::Q) return kr_prefix(Mersenne61{}, T, n, B, Hs, s);
   return kr_prefix(SmallMod{q}, T, n, B, Hs, s);
+}
+
+int expand_prefix(const uint8_t* T, uint64_t n, uint64_t B, uint64_t q, const uint64_t* Hs, uint64_t* H,
+                  cudaStream_t s) {
+  if (q == Mersenne61::Q) return kr_expand(Mersenne61{}, T, n, B, Hs, H, s);
+  return kr_expand(SmallMod{q}, T, n, B, Hs, H, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -31,7 +31,7 @@ from .workloads import Arrival
 def estimate_bytes(n: int) -> int:
     """Device footprint charged at admission: the text, build scratch and the
     tree (a conservative multiple of the text, plus fixed overheads)."""
-    return 48 * n + (64 << 20)
+    return 56 * n + (64 << 20)
 
 
 @dataclass

@@ -217,10 +217,12 @@ def _runs_text(n, seed, alphabet=b"ab", max_run=200):
     return np.frombuffer(bytes(out[:n]), np.uint8)
 
 
-@pytest.mark.parametrize("dense", [False, True])
-def test_anchored_and_dense_scans(dense):
+@pytest.mark.parametrize("scan", ["anchored", "dense", "tiny_queue"])
+def test_anchored_and_dense_scans(scan):
     """Both window-scan strategies give the oracle's tree, including texts whose
-    keys have no anchor (long runs) and short tails of every length."""
+    keys have no anchor (long runs) and short tails of every length; so does
+    the anchored scan whose candidate queue overflows at every level."""
+    kw = {"dense_scan": scan == "dense", "tiny_queue": scan == "tiny_queue"}
     cases = [
         (_runs_text(50_000, 1), 2, 8), (_runs_text(120_001, 2, b"abc", 500), 4, 16),
         (_runs_text(30_000, 3, b"a", 2), 2, 4), (np.full(100_003, 65, np.uint8), 4, 32),
@@ -232,7 +234,7 @@ def test_anchored_and_dense_scans(dense):
     for T, tau, leaf in cases:
         for prune in (True, False):
             ref = oracle.build(T, tau, leaf, prune=prune).export()
-            _, blob = gpu_export(T, 256, tau, leaf, prune=prune, dense_scan=dense)
+            _, blob = gpu_export(T, 256, tau, leaf, prune=prune, **kw)
             assert blob == ref, (len(T), tau, leaf, prune)
     rng = random.Random(7)
     for _ in range(150):
@@ -240,5 +242,5 @@ def test_anchored_and_dense_scans(dense):
         text = _random_text(rng, n, rng.choice([1, 2, 3, 26]))
         tau, leaf = rng.choice([2, 3, 4]), rng.choice([1, 3, 8, 40, 100])
         ref = oracle.build(text, tau, leaf).export()
-        _, blob = gpu_export(text, 256, tau, leaf, dense_scan=dense)
+        _, blob = gpu_export(text, 256, tau, leaf, **kw)
         assert blob == ref, (text, tau, leaf)
