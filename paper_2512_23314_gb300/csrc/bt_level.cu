@@ -410,6 +410,9 @@ struct ScanCtx {
   uint32_t* segn;                    // hits recorded by each scan CTA (may exceed seg)
   uint32_t seg;
   unsigned long long* qn;            // hits recorded in all
+  struct Cand* cq;                   // proposed windows: one segment of `cseg` entries per CTA
+  uint32_t* csegn;                   // windows proposed by each k_hits CTA (may exceed cseg)
+  uint32_t cseg;
   Status* status;                    // device-side invariant checks
 };
 
@@ -423,6 +426,14 @@ struct Hit {
   uint32_t mx;
 };
 constexpr uint64_t kHitSec = 1ull << 63;
+
+// A proposed window: start p and the end of the run span it lies in; the top
+// bit of `av` marks the short tail key (else a full-length key).
+struct Cand {
+  uint64_t p;
+  uint64_t av;
+};
+constexpr uint64_t kCandTail = 1ull << 63;
 
 // A full-length window at p (inside a run ending at av) matches slot sl;
 // Hb = H[p + b].  Updates the slot minimum and joins the pair starting here.
@@ -478,14 +489,21 @@ __device__ __forceinline__ void test_candidate(const ScanCtx<M>& C, uint64_t p, 
   }
 }
 
-// Test a proposed window that starts at p (kind 0: a full-length key, 1:
-// the short tail), if it lies inside a run.
+// A proposed window that starts at p (kind 0: a full-length key, 1: the
+// short tail), if it lies inside a run: queued in this CTA's candidate
+// segment (sq: its shared-memory counter), or tested here when sq is null.
 template <class M>
-__device__ __forceinline__ void propose(const ScanCtx<M>& C, uint64_t k, uint64_t s, uint64_t av, uint64_t p,
-                                        uint32_t kind, uint32_t& ncand, uint32_t& nhit) {
+__device__ __forceinline__ void propose(const ScanCtx<M>& C, unsigned int* sq, uint64_t k, uint64_t s,
+                                        uint64_t av, uint64_t p, uint32_t kind, uint32_t& ncand,
+                                        uint32_t& nhit) {
   uint64_t avp;
   if (!window_in_run(C.g, k, s, av, p, kind ? C.g.r : C.g.b, &avp)) return;
-  test_candidate(C, p, avp, kind, ncand, nhit);
+  if (!sq) {
+    test_candidate(C, p, avp, kind, ncand, nhit);
+    return;
+  }
+  const uint32_t idx = atomicAdd(sq, 1u);
+  if (idx < C.cseg) C.cq[blockIdx.x * (uint64_t)C.cseg + idx] = Cand{p, avp | (kind ? kCandTail : 0)};
 }
 
 // Record a hit in this CTA's segment (a shared-memory counter claims the
@@ -500,7 +518,7 @@ __device__ __forceinline__ void record_hit(const ScanCtx<M>& C, unsigned int* sq
 // The anchor-table lookup of a hit at x (mixed gram mx) in block k and the
 // test of every window its anchors propose.
 template <class M>
-__device__ __forceinline__ void anchor_hit(const ScanCtx<M>& C, const AnchorSet* __restrict__ atab,
+__device__ __forceinline__ void anchor_hit(const ScanCtx<M>& C, unsigned int* sq, const AnchorSet* __restrict__ atab,
                                            uint32_t amask, uint32_t tail_gram, uint32_t tail_a, uint64_t k,
                                            uint64_t s, uint64_t av, uint64_t x, uint32_t mx, uint32_t& ncand,
                                            uint32_t& nhit) {
@@ -539,7 +557,7 @@ __device__ __forceinline__ void anchor_hit(const ScanCtx<M>& C, const AnchorSet*
       pf = false;
       p = x - far;
     }
-    if (ok) propose(C, k, s, av, p, kind, ncand, nhit);
+    if (ok) propose(C, sq, k, s, av, p, kind, ncand, nhit);
   }
 }
 
@@ -815,7 +833,7 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_anchor(ScanCtx<M> C0, 
           const uint32_t i = 32 * G + bpos;
           const uint32_t jr = below + __popc(mg & ((1u << bpos) - 1u));
           const uint32_t mx = jr < exact ? ring[jr * kScanThreads] : gram_at(slot, i, w, rb);
-          if (INLINE) anchor_hit(C, atab, amask, tail_gram, tail_a, k, s, av, p0 + i, mx, ncand, nhit);
+          if (INLINE) anchor_hit(C, nullptr, atab, amask, tail_gram, tail_a, k, s, av, p0 + i, mx, ncand, nhit);
           else record_hit(C, &s_qn, p0 + i, k, mx);
         }
       }
@@ -833,7 +851,7 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_anchor(ScanCtx<M> C0, 
             } else {
 #pragma unroll 1
               for (uint32_t kind = 0; kind < 2; kind++)
-                if (kind ? tail_sec : anchorless) propose(C, k, s, av, p0 + i, kind, ncand, nhit);
+                if (kind ? tail_sec : anchorless) propose(C, nullptr, k, s, av, p0 + i, kind, ncand, nhit);
             }
           }
         }
@@ -853,14 +871,15 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_anchor(ScanCtx<M> C0, 
 }
 #undef BT_RECORD
 
-// The hits of scan CTA j's segment, one per thread: anchor-table lookup and
-// the test of every proposed window.
+// The hits of scan CTA j's segment, one per thread: anchor-table lookup; the
+// windows the anchors propose go to this CTA's candidate segment.
 template <class M>
 __global__ void __launch_bounds__(512) k_hits(ScanCtx<M> C0, const AnchorSet* __restrict__ atab,
                                               uint32_t amask) {
+  __shared__ unsigned int s_cn;
+  if (threadIdx.x == 0) s_cn = 0;
+  __syncthreads();
   ScanCtx<M> C = C0;
-  C.pretail = C.ld->pretail_slot;
-  C.fp_tail = C.ld->fp_tail;
   const Geo& g = C.g;
   const bool anchorless = C.ld->anchorless == 1u;
   const bool tail_sec = C.ld->tail_anchorless == 2u;
@@ -878,11 +897,80 @@ __global__ void __launch_bounds__(512) k_hits(ScanCtx<M> C0, const AnchorSet* __
     }
     const uint64_t k = e.k, s = g.st[k], av = avail_end(g, k);
     if (e.x & kHitSec) {
-      if (anchorless) propose(C, k, s, av, x, 0, ncand, nhit);
-      if (tail_sec) propose(C, k, s, av, x, 1, ncand, nhit);
+      if (anchorless) propose(C, &s_cn, k, s, av, x, 0, ncand, nhit);
+      if (tail_sec) propose(C, &s_cn, k, s, av, x, 1, ncand, nhit);
     } else {
-      anchor_hit(C, atab, amask, tail_gram, tail_a, k, s, av, x, e.mx, ncand, nhit);
+      anchor_hit(C, &s_cn, atab, amask, tail_gram, tail_a, k, s, av, x, e.mx, ncand, nhit);
     }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    C.csegn[blockIdx.x] = s_cn;
+    if (s_cn > C.cseg) C.ld->qover = 1u;
+  }
+}
+
+// Test the proposed windows of k_hits CTA j's segment, four per thread with
+// their loads in flight together.
+template <class M>
+__global__ void __launch_bounds__(256, 3) k_candidates(ScanCtx<M> C0) {
+  constexpr int U = 4;
+  ScanCtx<M> C = C0;
+  C.pretail = C.ld->pretail_slot;
+  C.fp_tail = C.ld->fp_tail;
+  const Geo& g = C.g;
+  const uint32_t sn = C.csegn[blockIdx.x];
+  const uint64_t n = sn < C.cseg ? sn : C.cseg;
+  const Cand* q = C.cq + blockIdx.x * (uint64_t)C.cseg;
+  uint32_t ncand = 0, nhit = 0;
+  const unsigned lane = threadIdx.x & 31;
+  for (uint64_t base = (threadIdx.x & ~31u) * (uint64_t)U; base < n; base += (uint64_t)blockDim.x * U) {
+    const uint64_t i0 = base + lane * U;
+    Cand e[U];
+    uint64_t H0[U], H1[U], fp[U], slot[U], key[U];
+    bool blk[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      blk[u] = false;
+      if (i0 + u < n) {
+        e[u] = q[i0 + u];
+        const uint64_t av = e[u].av & ~kCandTail;
+        if (av > g.n || e[u].p + ((e[u].av & kCandTail) ? g.r : g.b) > av) {  // invariant check
+          atomicExch(&C.status->error, 9ull);
+          continue;
+        }
+        if (e[u].av & kCandTail) {
+          if (window_fast(C.m, g.H, g.Br, e[u].p, g.r) == C.fp_tail) min_pos(&C.ld->lo_tail, e[u].p);
+        } else {
+          blk[u] = true;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      if (blk[u]) {
+        H0[u] = g.H[e[u].p];
+        H1[u] = g.H[e[u].p + g.b];
+      }
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      if (blk[u]) {
+        ncand++;
+        fp[u] = C.m.sub(H1[u], C.m.mul(H0[u], g.Bb));
+        slot[u] = mix64(fp[u]) & C.bmask;
+        key[u] = C.bkey[slot[u]];
+      }
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      if (blk[u]) {
+        uint32_t sl = kNoSlot;
+        if (key[u] == fp[u]) sl = (uint32_t)slot[u];
+        else if (key[u] != kNone) sl = tbl_find(C.bkey, C.bmask, fp[u]);
+        if (sl != kNoSlot) {
+          nhit++;
+          on_block_hit(C, sl, e[u].p, e[u].av, H1[u]);
+        }
+      }
   }
   if (ncand) atomicAdd(&C.ld->cands, (unsigned long long)ncand);
   if (nhit) atomicAdd(&C.ld->hits, (unsigned long long)nhit);
@@ -1428,6 +1516,8 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
   uint32_t *bitmap = nullptr, *secbits = nullptr, *sagg = nullptr;
   Hit* q = nullptr;
   uint32_t* segn = nullptr;
+  Cand* cq = nullptr;
+  uint32_t* csegn = nullptr;
   unsigned long long* qn = nullptr;
   auto carve = [&]() {
     W.fpB = A.take<uint64_t>(c);
@@ -1455,6 +1545,8 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
       secbits = A.take<uint32_t>(kSecBits / 32);
       q = A.take<Hit>((uint64_t)seg * scan_grid);
       segn = A.take<uint32_t>(scan_grid);
+      cq = A.take<Cand>((uint64_t)seg * scan_grid);
+      csegn = A.take<uint32_t>(scan_grid);
       qn = A.take<unsigned long long>(1);
     }
   };
@@ -1496,7 +1588,7 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
     BT_LAUNCH(k_anchor_keys<<<gc, T, 0, s>>>(g, gq, W.slotB, atab, (uint32_t)(acap - 1), bitmap, secbits,
                                              W.ld, ctx.st));
     ScanCtx<M> C{m, g, W.bkey, bcap - 1, W.blo, W.pkey, pcap - 1, W.plo, W.ld, 0, 0, W.maxpst,
-                 q, segn, seg, qn, ctx.st};
+                 q, segn, seg, qn, cq, csegn, seg, ctx.st};
     const size_t smem_base = ((size_t)kSecBits / 32 + (size_t)kRing * kScanThreads +
                               (size_t)kScanThreads * kSlotWords) * 4;
     const size_t smem = smem_base + (size_t)bm_smem * 4;
@@ -1508,6 +1600,7 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
     BT_LAUNCH(k_scan_anchor<M, false><<<scan_grid, kScanThreads, smem, s>>>(
         C, gq, cpa, atab, (uint32_t)(acap - 1), bitmap, bm_smem, secbits));
     BT_LAUNCH(k_hits<M><<<scan_grid, 512, 0, s>>>(C, atab, (uint32_t)(acap - 1)));
+    BT_LAUNCH(k_candidates<M><<<scan_grid, 256, 0, s>>>(C));
     // Only when the queue overflowed: the scan again, testing windows inline.
     BT_LAUNCH(k_scan_anchor<M, true><<<scan_grid, kScanThreads, smem, s>>>(
         C, gq, cpa, atab, (uint32_t)(acap - 1), bitmap, bm_smem, secbits));
