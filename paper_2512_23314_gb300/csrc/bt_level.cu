@@ -444,7 +444,7 @@ __device__ __forceinline__ void on_block_hit(const ScanCtx<M>& C, uint32_t sl, u
   min_pos(&C.blo[sl], p);
   if (p > C.maxpst[sl]) return;  // no pair starting with this slot can begin here or later
   if (p + 2 * g.b <= av) {
-    const uint64_t fp2 = C.m.sub(g.H[p + 2 * g.b], C.m.mul(Hb, g.Bb));
+    const uint64_t fp2 = C.m.sub(__ldcs(g.H + p + 2 * g.b), C.m.mul(Hb, g.Bb));
     const uint32_t s2 = tbl_find(C.bkey, C.bmask, fp2);
     if (s2 != kNoSlot) {
       const uint32_t ps = tbl_find(C.pkey, C.pmask, ((uint64_t)sl << 32) | s2);
@@ -480,8 +480,8 @@ __device__ __forceinline__ void test_candidate(const ScanCtx<M>& C, uint64_t p, 
     return;
   }
   ncand++;
-  const uint64_t Hb = g.H[p + g.b];
-  const uint64_t fp = C.m.sub(Hb, C.m.mul(g.H[p], g.Bb));
+  const uint64_t Hb = __ldcs(g.H + p + g.b);
+  const uint64_t fp = C.m.sub(Hb, C.m.mul(__ldcs(g.H + p), g.Bb));
   const uint32_t sl = tbl_find(C.bkey, C.bmask, fp);
   if (sl != kNoSlot) {
     nhit++;
@@ -910,8 +910,14 @@ __global__ void __launch_bounds__(512) k_hits(ScanCtx<M> C0, const AnchorSet* __
   }
 }
 
-// Test the proposed windows of k_hits CTA j's segment, four per thread with
-// their loads in flight together.
+// Test the proposed windows of k_hits CTA j's segment, four per thread, in
+// phases whose loads are all in flight together: the prefix fingerprints at
+// p and p+b, the block-table probe; for the windows that match a block, the
+// slot minimum (an atomic without return), the last pair start of the slot
+// and the prefix fingerprint at p+2b; then the probe of the block at p+b and
+// of the pair table.  Prefix fingerprints are read with the streaming
+// (evict-first) hint: random and used once, they should not push the tables
+// out of L2.
 template <class M>
 __global__ void __launch_bounds__(256, 3) k_candidates(ScanCtx<M> C0) {
   constexpr int U = 4;
@@ -926,50 +932,91 @@ __global__ void __launch_bounds__(256, 3) k_candidates(ScanCtx<M> C0) {
   const unsigned lane = threadIdx.x & 31;
   for (uint64_t base = (threadIdx.x & ~31u) * (uint64_t)U; base < n; base += (uint64_t)blockDim.x * U) {
     const uint64_t i0 = base + lane * U;
-    Cand e[U];
-    uint64_t H0[U], H1[U], fp[U], slot[U], key[U];
-    bool blk[U];
+    uint64_t p[U], av[U], H1[U], x[U], y[U];
+    uint32_t sl[U];
+    bool live[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
-      blk[u] = false;
+      live[u] = false;
+      sl[u] = kNoSlot;
       if (i0 + u < n) {
-        e[u] = q[i0 + u];
-        const uint64_t av = e[u].av & ~kCandTail;
-        if (av > g.n || e[u].p + ((e[u].av & kCandTail) ? g.r : g.b) > av) {  // invariant check
+        const Cand e = q[i0 + u];
+        p[u] = e.p;
+        av[u] = e.av & ~kCandTail;
+        if (av[u] > g.n || e.p + ((e.av & kCandTail) ? g.r : g.b) > av[u]) {  // invariant check
           atomicExch(&C.status->error, 9ull);
           continue;
         }
-        if (e[u].av & kCandTail) {
-          if (window_fast(C.m, g.H, g.Br, e[u].p, g.r) == C.fp_tail) min_pos(&C.ld->lo_tail, e[u].p);
+        if (e.av & kCandTail) {
+          if (window_fast(C.m, g.H, g.Br, e.p, g.r) == C.fp_tail) min_pos(&C.ld->lo_tail, e.p);
         } else {
-          blk[u] = true;
+          live[u] = true;
         }
       }
     }
+    // Window fingerprints and the first block-table probe.
 #pragma unroll
     for (int u = 0; u < U; u++)
-      if (blk[u]) {
-        H0[u] = g.H[e[u].p];
-        H1[u] = g.H[e[u].p + g.b];
+      if (live[u]) {
+        x[u] = __ldcs(g.H + p[u]);
+        H1[u] = __ldcs(g.H + p[u] + g.b);
       }
 #pragma unroll
     for (int u = 0; u < U; u++)
-      if (blk[u]) {
+      if (live[u]) {
         ncand++;
-        fp[u] = C.m.sub(H1[u], C.m.mul(H0[u], g.Bb));
-        slot[u] = mix64(fp[u]) & C.bmask;
-        key[u] = C.bkey[slot[u]];
+        x[u] = C.m.sub(H1[u], C.m.mul(x[u], g.Bb));  // x: the window's fingerprint
+        y[u] = mix64(x[u]) & C.bmask;                  // y: its first slot
+        sl[u] = (uint32_t)y[u];
+        y[u] = C.bkey[y[u]];                           // y: the key there
       }
 #pragma unroll
     for (int u = 0; u < U; u++)
-      if (blk[u]) {
-        uint32_t sl = kNoSlot;
-        if (key[u] == fp[u]) sl = (uint32_t)slot[u];
-        else if (key[u] != kNone) sl = tbl_find(C.bkey, C.bmask, fp[u]);
-        if (sl != kNoSlot) {
-          nhit++;
-          on_block_hit(C, sl, e[u].p, e[u].av, H1[u]);
+      if (live[u]) {
+        if (y[u] != x[u]) sl[u] = y[u] == kNone ? kNoSlot : tbl_find(C.bkey, C.bmask, x[u]);
+        live[u] = sl[u] != kNoSlot;
+      }
+    // Block hits: slot minimum, pair start bound, prefix fingerprint at p+2b.
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      if (live[u]) {
+        nhit++;
+        atomicMin(&C.blo[sl[u]], (unsigned long long)p[u]);
+        x[u] = C.maxpst[sl[u]];
+        y[u] = p[u] + 2 * g.b <= av[u] ? __ldcs(g.H + p[u] + 2 * g.b) : kNone;
+      }
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      if (live[u]) {
+        // The short tail pair (rare: only the block before the tail).
+        if (g.r && sl[u] == C.pretail && p[u] + g.b + g.r <= av[u] &&
+            window_fast(C.m, g.H, g.Br, p[u] + g.b, g.r) == C.fp_tail)
+          min_pos(&C.ld->lo_tailpair, p[u]);
+        live[u] = p[u] <= x[u] && y[u] != kNone;  // a pair starting with this slot can begin here
+        if (live[u]) {
+          x[u] = C.m.sub(y[u], C.m.mul(H1[u], g.Bb));  // fingerprint of the block at p+b
+          y[u] = mix64(x[u]) & C.bmask;
+          H1[u] = C.bkey[y[u]];
         }
+      }
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      if (live[u]) {
+        uint32_t s2 = (uint32_t)y[u];
+        if (H1[u] != x[u]) s2 = H1[u] == kNone ? kNoSlot : tbl_find(C.bkey, C.bmask, x[u]);
+        live[u] = s2 != kNoSlot;
+        if (live[u]) {
+          x[u] = ((uint64_t)sl[u] << 32) | s2;  // the pair key
+          y[u] = mix64(x[u]) & C.pmask;
+          H1[u] = C.pkey[y[u]];
+        }
+      }
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      if (live[u]) {
+        uint32_t ps = (uint32_t)y[u];
+        if (H1[u] != x[u]) ps = H1[u] == kNone ? kNoSlot : tbl_find(C.pkey, C.pmask, x[u]);
+        if (ps != kNoSlot) atomicMin(&C.plo[ps], (unsigned long long)p[u]);
       }
   }
   if (ncand) atomicAdd(&C.ld->cands, (unsigned long long)ncand);
