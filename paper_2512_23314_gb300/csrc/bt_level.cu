@@ -96,22 +96,39 @@ __device__ __forceinline__ uint64_t avail_end(const Geo& g, uint64_t k) {
   return e;
 }
 
-__device__ __forceinline__ uint32_t tbl_insert(uint64_t* keys, uint64_t mask, uint64_t key) {
+// One block-table slot, one 32-byte sector: the key (a block fingerprint),
+// the leftmost window seen with that fingerprint, and the last start of a
+// pair whose first block has this slot.  A probe, its minimum update and the
+// pair bound touch the same sector.
+struct __align__(32) BSlot {
+  unsigned long long key;
+  unsigned long long lo;
+  unsigned long long maxpst;
+  unsigned long long pad;
+};
+// One pair-table slot: the key (the two block slots) and the leftmost window.
+struct __align__(16) PSlot {
+  unsigned long long key;
+  unsigned long long lo;
+};
+
+// Open addressing with linear probing on the slots' keys.
+template <class S>
+__device__ __forceinline__ uint32_t tbl_insert(S* t, uint64_t mask, uint64_t key) {
   uint64_t h = mix64(key) & mask;
   for (uint64_t it = 0; it <= mask; it++) {
-    unsigned long long old = atomicCAS((unsigned long long*)&keys[h], (unsigned long long)kNone,
-                                       (unsigned long long)key);
+    unsigned long long old = atomicCAS(&t[h].key, (unsigned long long)kNone, (unsigned long long)key);
     if (old == kNone || old == key) return (uint32_t)h;
     h = (h + 1) & mask;
   }
   return kNoSlot;
 }
 
-__device__ __forceinline__ uint32_t tbl_find(const uint64_t* __restrict__ keys, uint64_t mask,
-                                             uint64_t key) {
+template <class S>
+__device__ __forceinline__ uint32_t tbl_find(const S* __restrict__ t, uint64_t mask, uint64_t key) {
   uint64_t h = mix64(key) & mask;
   for (uint64_t it = 0; it <= mask; it++) {
-    uint64_t k = keys[h];
+    uint64_t k = t[h].key;
     if (k == key) return (uint32_t)h;
     if (k == kNone) return kNoSlot;
     h = (h + 1) & mask;
@@ -145,22 +162,20 @@ __device__ __forceinline__ uint64_t warp_sum(uint64_t v) {
 // 1. Block fingerprints and block-table insertion.
 template <class M>
 __global__ void k_block_fp(M m, Geo g, uint64_t* __restrict__ fpB, uint32_t* __restrict__ slotB,
-                           uint64_t* bkey, uint64_t bmask, uint32_t* brep, LevelDev* ld,
-                           Status* status) {
+                           BSlot* bt, uint64_t bmask, LevelDev* ld, Status* status) {
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < g.c;
        k += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t s = g.st[k], len = blen(g, k);
     uint64_t fp = window_fast(m, g.H, len == g.b ? g.Bb : g.Br, s, len);
     fpB[k] = fp;
     if (len == g.b) {
-      uint32_t slot = tbl_insert(bkey, bmask, fp);
+      uint32_t slot = tbl_insert(bt, bmask, fp);
       if (slot == kNoSlot) {
         atomicExch(&status->error, 1ull);
         slotB[k] = kNoSlot;
         continue;
       }
       slotB[k] = slot;
-      atomicMin(&brep[slot], (uint32_t)k);
     } else {
       slotB[k] = kNoSlot;
       ld->fp_tail = fp;
@@ -170,8 +185,7 @@ __global__ void k_block_fp(M m, Geo g, uint64_t* __restrict__ fpB, uint32_t* __r
 
 // 2. Pair-table insertion: key (slot_k, slot_k+1) for pairs of full blocks.
 __global__ void k_pair_insert(Geo g, const uint32_t* __restrict__ slotB, uint32_t* __restrict__ slotP,
-                              uint64_t* pkey, uint64_t pmask, unsigned long long* maxpst, LevelDev* ld,
-                              Status* status) {
+                              PSlot* pt, uint64_t pmask, BSlot* bt, LevelDev* ld, Status* status) {
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k + 1 < g.c;
        k += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t sp = kNoSlot;
@@ -179,12 +193,12 @@ __global__ void k_pair_insert(Geo g, const uint32_t* __restrict__ slotB, uint32_
       atomicAdd(&ld->npairs, 1u);
       // The last pair start per first-block slot: a window after it cannot
       // be the leftmost occurrence of any pair that starts with that slot.
-      if (slotB[k] != kNoSlot) atomicMax(&maxpst[slotB[k]], (unsigned long long)g.st[k]);
+      if (slotB[k] != kNoSlot) atomicMax(&bt[slotB[k]].maxpst, (unsigned long long)g.st[k]);
       if (slotB[k + 1] == kNoSlot) {
         sp = kTailPair;
         ld->pretail_slot = slotB[k];
       } else {
-        sp = tbl_insert(pkey, pmask, ((uint64_t)slotB[k] << 32) | slotB[k + 1]);
+        sp = tbl_insert(pt, pmask, ((uint64_t)slotB[k] << 32) | slotB[k + 1]);
         if (sp == kNoSlot) atomicExch(&status->error, 2ull);
       }
     }
@@ -197,10 +211,8 @@ __global__ void k_pair_insert(Geo g, const uint32_t* __restrict__ slotB, uint32_
 // could not cover the tail key (it has no anchor).
 template <class M>
 __global__ void __launch_bounds__(256) k_scan(M m, Geo g, uint64_t cpb,
-                                             const uint64_t* __restrict__ bkey, uint64_t bmask,
-                                             unsigned long long* blo,
-                                             const uint64_t* __restrict__ pkey, uint64_t pmask,
-                                             unsigned long long* plo, LevelDev* ld, int tail_only) {
+                                             BSlot* bt, uint64_t bmask, PSlot* pt, uint64_t pmask,
+                                             LevelDev* ld, int tail_only) {
   if (tail_only && ld->tail_anchorless != 1u) return;  // 1: the tail is shorter than a gram
   const uint64_t total = g.c * cpb;
   const uint32_t pretail = ld->pretail_slot;
@@ -220,15 +232,15 @@ __global__ void __launch_bounds__(256) k_scan(M m, Geo g, uint64_t cpb,
           uint64_t out = (uint64_t)g.T[p - 1] + 1, in = (uint64_t)g.T[p + g.b - 1] + 1;
           fp = m.add(m.sub(m.mul(fp, g.B), m.mul(out, g.Bb)), in);
         }
-        uint32_t sl = tbl_find(bkey, bmask, fp);
+        uint32_t sl = tbl_find(bt, bmask, fp);
         if (sl == kNoSlot) continue;
-        min_pos(&blo[sl], p);
+        min_pos(&bt[sl].lo, p);
         if (p + 2 * g.b <= av) {
           uint64_t fp2 = window_fast(m, g.H, g.Bb, p + g.b, g.b);
-          uint32_t s2 = tbl_find(bkey, bmask, fp2);
+          uint32_t s2 = tbl_find(bt, bmask, fp2);
           if (s2 != kNoSlot) {
-            uint32_t ps = tbl_find(pkey, pmask, ((uint64_t)sl << 32) | s2);
-            if (ps != kNoSlot) min_pos(&plo[ps], p);
+            uint32_t ps = tbl_find(pt, pmask, ((uint64_t)sl << 32) | s2);
+            if (ps != kNoSlot) min_pos(&pt[ps].lo, p);
           }
         }
         if (g.r && sl == pretail && p + g.b + g.r <= av &&
@@ -396,16 +408,13 @@ template <class M>
 struct ScanCtx {
   M m;
   Geo g;
-  const uint64_t* bkey;
+  BSlot* bt;
   uint64_t bmask;
-  unsigned long long* blo;
-  const uint64_t* pkey;
+  PSlot* pt;
   uint64_t pmask;
-  unsigned long long* plo;
   LevelDev* ld;
   uint32_t pretail;
   uint64_t fp_tail;
-  const unsigned long long* maxpst;  // last pair start per first-block slot
   struct Hit* q;                     // gram hits: one segment of `seg` entries per scan CTA
   uint32_t* segn;                    // hits recorded by each scan CTA (may exceed seg)
   uint32_t seg;
@@ -441,14 +450,14 @@ template <class M>
 __device__ __forceinline__ void on_block_hit(const ScanCtx<M>& C, uint32_t sl, uint64_t p, uint64_t av,
                                              uint64_t Hb) {
   const Geo& g = C.g;
-  min_pos(&C.blo[sl], p);
-  if (p > C.maxpst[sl]) return;  // no pair starting with this slot can begin here or later
+  min_pos(&C.bt[sl].lo, p);
+  if (p > C.bt[sl].maxpst) return;  // no pair starting with this slot can begin here or later
   if (p + 2 * g.b <= av) {
     const uint64_t fp2 = C.m.sub(__ldcs(g.H + p + 2 * g.b), C.m.mul(Hb, g.Bb));
-    const uint32_t s2 = tbl_find(C.bkey, C.bmask, fp2);
+    const uint32_t s2 = tbl_find(C.bt, C.bmask, fp2);
     if (s2 != kNoSlot) {
-      const uint32_t ps = tbl_find(C.pkey, C.pmask, ((uint64_t)sl << 32) | s2);
-      if (ps != kNoSlot) min_pos(&C.plo[ps], p);
+      const uint32_t ps = tbl_find(C.pt, C.pmask, ((uint64_t)sl << 32) | s2);
+      if (ps != kNoSlot) min_pos(&C.pt[ps].lo, p);
     }
   }
   if (g.r && sl == C.pretail && p + g.b + g.r <= av &&
@@ -482,7 +491,7 @@ __device__ __forceinline__ void test_candidate(const ScanCtx<M>& C, uint64_t p, 
   ncand++;
   const uint64_t Hb = __ldcs(g.H + p + g.b);
   const uint64_t fp = C.m.sub(Hb, C.m.mul(__ldcs(g.H + p), g.Bb));
-  const uint32_t sl = tbl_find(C.bkey, C.bmask, fp);
+  const uint32_t sl = tbl_find(C.bt, C.bmask, fp);
   if (sl != kNoSlot) {
     nhit++;
     on_block_hit(C, sl, p, avp, Hb);
@@ -968,12 +977,12 @@ __global__ void __launch_bounds__(256, 3) k_candidates(ScanCtx<M> C0) {
         x[u] = C.m.sub(H1[u], C.m.mul(x[u], g.Bb));  // x: the window's fingerprint
         y[u] = mix64(x[u]) & C.bmask;                  // y: its first slot
         sl[u] = (uint32_t)y[u];
-        y[u] = C.bkey[y[u]];                           // y: the key there
+        y[u] = C.bt[y[u]].key;                         // y: the key there
       }
 #pragma unroll
     for (int u = 0; u < U; u++)
       if (live[u]) {
-        if (y[u] != x[u]) sl[u] = y[u] == kNone ? kNoSlot : tbl_find(C.bkey, C.bmask, x[u]);
+        if (y[u] != x[u]) sl[u] = y[u] == kNone ? kNoSlot : tbl_find(C.bt, C.bmask, x[u]);
         live[u] = sl[u] != kNoSlot;
       }
     // Block hits: slot minimum, pair start bound, prefix fingerprint at p+2b.
@@ -981,8 +990,8 @@ __global__ void __launch_bounds__(256, 3) k_candidates(ScanCtx<M> C0) {
     for (int u = 0; u < U; u++)
       if (live[u]) {
         nhit++;
-        atomicMin(&C.blo[sl[u]], (unsigned long long)p[u]);
-        x[u] = C.maxpst[sl[u]];
+        atomicMin(&C.bt[sl[u]].lo, (unsigned long long)p[u]);
+        x[u] = C.bt[sl[u]].maxpst;
         y[u] = p[u] + 2 * g.b <= av[u] ? __ldcs(g.H + p[u] + 2 * g.b) : kNone;
       }
 #pragma unroll
@@ -996,27 +1005,27 @@ __global__ void __launch_bounds__(256, 3) k_candidates(ScanCtx<M> C0) {
         if (live[u]) {
           x[u] = C.m.sub(y[u], C.m.mul(H1[u], g.Bb));  // fingerprint of the block at p+b
           y[u] = mix64(x[u]) & C.bmask;
-          H1[u] = C.bkey[y[u]];
+          H1[u] = C.bt[y[u]].key;
         }
       }
 #pragma unroll
     for (int u = 0; u < U; u++)
       if (live[u]) {
         uint32_t s2 = (uint32_t)y[u];
-        if (H1[u] != x[u]) s2 = H1[u] == kNone ? kNoSlot : tbl_find(C.bkey, C.bmask, x[u]);
+        if (H1[u] != x[u]) s2 = H1[u] == kNone ? kNoSlot : tbl_find(C.bt, C.bmask, x[u]);
         live[u] = s2 != kNoSlot;
         if (live[u]) {
           x[u] = ((uint64_t)sl[u] << 32) | s2;  // the pair key
           y[u] = mix64(x[u]) & C.pmask;
-          H1[u] = C.pkey[y[u]];
+          H1[u] = C.pt[y[u]].key;
         }
       }
 #pragma unroll
     for (int u = 0; u < U; u++)
       if (live[u]) {
         uint32_t ps = (uint32_t)y[u];
-        if (H1[u] != x[u]) ps = H1[u] == kNone ? kNoSlot : tbl_find(C.pkey, C.pmask, x[u]);
-        if (ps != kNoSlot) atomicMin(&C.plo[ps], (unsigned long long)p[u]);
+        if (H1[u] != x[u]) ps = H1[u] == kNone ? kNoSlot : tbl_find(C.pt, C.pmask, x[u]);
+        if (ps != kNoSlot) atomicMin(&C.pt[ps].lo, (unsigned long long)p[u]);
       }
   }
   if (ncand) atomicAdd(&C.ld->cands, (unsigned long long)ncand);
@@ -1026,7 +1035,7 @@ __global__ void __launch_bounds__(256, 3) k_candidates(ScanCtx<M> C0) {
 // 4a. Pair results: leftmost when the slot minimum is the pair's own start;
 // otherwise queue a verification of the earlier occurrence.
 __global__ void k_pair_jobs(Geo g, const uint32_t* __restrict__ slotP,
-                            const unsigned long long* __restrict__ plo, uint64_t* __restrict__ plo_k,
+                            const PSlot* __restrict__ pt, uint64_t* __restrict__ plo_k,
                             uint8_t* __restrict__ pm, Job* jobs, uint64_t* job_of, LevelDev* ld,
                             Status* status) {
   const uint64_t np = g.c ? g.c - 1 : 0;
@@ -1041,7 +1050,7 @@ __global__ void k_pair_jobs(Geo g, const uint32_t* __restrict__ slotP,
       pm[k] = 0;
       job_of[k] = kNone;
       if (sp != kNoSlot) {
-        lo = sp == kTailPair ? ld->lo_tailpair : plo[sp];
+        lo = sp == kTailPair ? ld->lo_tailpair : pt[sp].lo;
         s = g.st[k];
         plo_k[k] = lo;
         if (lo == s) {
@@ -1187,7 +1196,7 @@ __device__ __forceinline__ bool is_marked(const uint32_t* mw, uint64_t k) {
 // 6a. Block leftmost occurrences: unmarked blocks always (they become
 // pointers), marked blocks too when pruning needs them.
 __global__ void k_block_jobs(Geo g, const uint32_t* __restrict__ slotB,
-                             const unsigned long long* __restrict__ blo, const uint32_t* __restrict__ mw,
+                             const BSlot* __restrict__ bt, const uint32_t* __restrict__ mw,
                              int all, uint64_t* __restrict__ lo, Job* jobs, uint64_t* job_of,
                              LevelDev* ld, Status* status) {
   const unsigned lane = threadIdx.x & 31;
@@ -1202,7 +1211,7 @@ __global__ void k_block_jobs(Geo g, const uint32_t* __restrict__ slotB,
       if (all || !is_marked(mw, k)) {
         s = g.st[k];
         len = blen(g, k);
-        p = slotB[k] == kNoSlot ? ld->lo_tail : blo[slotB[k]];
+        p = slotB[k] == kNoSlot ? ld->lo_tail : bt[slotB[k]].lo;
         lo[k] = p;
         if (p < s) want = true;
         else if (p > s) atomicExch(&status->error, 4ull);
@@ -1320,13 +1329,9 @@ __global__ void k_level_start(uint64_t c, uint64_t b, uint64_t* st) {
 }
 
 struct InitArgs {
-  uint64_t* bkey;
-  uint32_t* brep;
-  unsigned long long* blo;
-  unsigned long long* maxpst;
+  BSlot* bt;
   uint64_t bcap;
-  uint64_t* pkey;
-  unsigned long long* plo;
+  PSlot* pt;
   uint64_t pcap;
   unsigned int* mismatch;
   uint64_t c;
@@ -1348,16 +1353,8 @@ __global__ void k_level_init(InitArgs a) {
   if (a.bwords > top) top = a.bwords;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < top;
        i += (uint64_t)gridDim.x * blockDim.x) {
-    if (i < a.bcap) {
-      a.bkey[i] = kNone;
-      a.brep[i] = 0xFFFFFFFFu;
-      a.blo[i] = kNone;
-      a.maxpst[i] = 0;
-    }
-    if (i < a.pcap) {
-      a.pkey[i] = kNone;
-      a.plo[i] = kNone;
-    }
+    if (i < a.bcap) a.bt[i] = BSlot{kNone, kNone, 0, 0};
+    if (i < a.pcap) a.pt[i] = PSlot{kNone, kNone};
     if (i < a.c) a.mismatch[i] = 0;
     if (a.atab && i < a.acap) {
       a.atab[i].gram = kEmptyGram;
@@ -1481,10 +1478,11 @@ uint64_t pow2_at_least(uint64_t x) {
 }
 
 struct LevelWork {
-  uint64_t *fpB, *bkey, *pkey, *plo_k, *job_of, *susp;
-  unsigned long long* maxpst;
-  uint32_t *slotB, *brep, *slotP, *wpop;
-  unsigned long long *blo, *plo, *exlo;
+  uint64_t *fpB, *plo_k, *job_of, *susp;
+  BSlot* bt;
+  PSlot* pt;
+  uint32_t *slotB, *slotP, *wpop;
+  unsigned long long* exlo;
   uint8_t* pm;
   Job* jobs;
   unsigned int* mismatch;
@@ -1577,12 +1575,8 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
     W.exlo = A.take<unsigned long long>(c);
     W.jobs = A.take<Job>(c);
     W.mismatch = A.take<unsigned int>(c);
-    W.bkey = A.take<uint64_t>(bcap);
-    W.brep = A.take<uint32_t>(bcap);
-    W.blo = A.take<unsigned long long>(bcap);
-    W.maxpst = A.take<unsigned long long>(bcap);
-    W.pkey = A.take<uint64_t>(pcap);
-    W.plo = A.take<unsigned long long>(pcap);
+    W.bt = A.take<BSlot>(bcap);
+    W.pt = A.take<PSlot>(pcap);
     W.ld = A.take<LevelDev>(1);
     W.wpop = A.take<uint32_t>(words);
     sagg = A.take<uint32_t>(scan_scratch_words(words));
@@ -1617,24 +1611,24 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
     v.lo = (uint64_t*)(mem + o_lo);
   }
 
-  InitArgs ia{W.bkey, W.brep, W.blo, W.maxpst, bcap, W.pkey, W.plo, pcap, W.mismatch, c,
+  InitArgs ia{W.bt, bcap, W.pt, pcap, W.mismatch, c,
               atab, acap, bitmap, bwords, secbits, qn, W.ld};
   {
     uint64_t top = bcap > acap ? bcap : acap;
     if (bwords > top) top = bwords;
     BT_LAUNCH(k_level_init<<<grid_for(top, T), T, 0, s>>>(ia));
   }
-  BT_LAUNCH(k_block_fp<M><<<gc, T, 0, s>>>(m, g, W.fpB, W.slotB, W.bkey, bcap - 1, W.brep, W.ld, ctx.st));
-  BT_LAUNCH(k_pair_insert<<<gc, T, 0, s>>>(g, W.slotB, W.slotP, W.pkey, pcap - 1, W.maxpst, W.ld,
+  BT_LAUNCH(k_block_fp<M><<<gc, T, 0, s>>>(m, g, W.fpB, W.slotB, W.bt, bcap - 1, W.ld, ctx.st));
+  BT_LAUNCH(k_pair_insert<<<gc, T, 0, s>>>(g, W.slotB, W.slotP, W.pt, pcap - 1, W.bt, W.ld,
                                            ctx.st));
   if (!anchored) {
     ProfScope ps("window_scan", s, cov_l);
-    BT_LAUNCH(k_scan<M><<<grid_for(c * cpb, T), T, 0, s>>>(m, g, cpb, W.bkey, bcap - 1, W.blo, W.pkey,
-                                                            pcap - 1, W.plo, W.ld, 0));
+    BT_LAUNCH(k_scan<M><<<grid_for(c * cpb, T), T, 0, s>>>(m, g, cpb, W.bt, bcap - 1, W.pt, pcap - 1,
+                                                            W.ld, 0));
   } else {
     BT_LAUNCH(k_anchor_keys<<<gc, T, 0, s>>>(g, gq, W.slotB, atab, (uint32_t)(acap - 1), bitmap, secbits,
                                              W.ld, ctx.st));
-    ScanCtx<M> C{m, g, W.bkey, bcap - 1, W.blo, W.pkey, pcap - 1, W.plo, W.ld, 0, 0, W.maxpst,
+    ScanCtx<M> C{m, g, W.bt, bcap - 1, W.pt, pcap - 1, W.ld, 0, 0,
                  q, segn, seg, qn, cq, csegn, seg, ctx.st};
     const size_t smem_base = ((size_t)kSecBits / 32 + (size_t)kRing * kScanThreads +
                               (size_t)kScanThreads * kSlotWords) * 4;
@@ -1652,14 +1646,14 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
     BT_LAUNCH(k_scan_anchor<M, true><<<scan_grid, kScanThreads, smem, s>>>(
         C, gq, cpa, atab, (uint32_t)(acap - 1), bitmap, bm_smem, secbits));
     if (r)
-      BT_LAUNCH(k_scan<M><<<grid_for(c * cpb, T), T, 0, s>>>(m, g, cpb, W.bkey, bcap - 1, W.blo, W.pkey,
-                                                              pcap - 1, W.plo, W.ld, 1));
+      BT_LAUNCH(k_scan<M><<<grid_for(c * cpb, T), T, 0, s>>>(m, g, cpb, W.bt, bcap - 1, W.pt, pcap - 1,
+                                                              W.ld, 1));
   }
   BT_CUDA(cudaGetLastError());
 
   // Pairs: verify, resolve collisions exactly, mark.
   const uint64_t ppj_pair = (2 * b + kPiece - 1) / kPiece;
-  BT_LAUNCH(k_pair_jobs<<<gc, T, 0, s>>>(g, W.slotP, W.plo, W.plo_k, W.pm, W.jobs, W.job_of, W.ld, ctx.st));
+  BT_LAUNCH(k_pair_jobs<<<gc, T, 0, s>>>(g, W.slotP, W.pt, W.plo_k, W.pm, W.jobs, W.job_of, W.ld, ctx.st));
   BT_LAUNCH(k_verify<<<grid_for(c * ppj_pair * 32, T), T, 0, s>>>(ctx.T, W.jobs, W.ld, ppj_pair, W.mismatch));
   BT_LAUNCH(k_pair_apply<<<gc, T, 0, s>>>(g, W.job_of, W.mismatch, W.susp, W.exlo, W.ld, ctx.st));
   BT_TRY(exact_pass(m, g, cpb, 1, W, s));
@@ -1671,7 +1665,7 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
   // Blocks: leftmost occurrences, verified; pointers.
   BT_LAUNCH(k_reset_jobs<<<gc, T, 0, s>>>(W.mismatch, c, W.ld));
   const uint64_t ppj_blk = (b + kPiece - 1) / kPiece;
-  BT_LAUNCH(k_block_jobs<<<gc, T, 0, s>>>(g, W.slotB, W.blo, v.mw, t->prune, v.lo, W.jobs, W.job_of, W.ld,
+  BT_LAUNCH(k_block_jobs<<<gc, T, 0, s>>>(g, W.slotB, W.bt, v.mw, t->prune, v.lo, W.jobs, W.job_of, W.ld,
                                 ctx.st));
   BT_LAUNCH(k_verify<<<grid_for(c * ppj_blk * 32, T), T, 0, s>>>(ctx.T, W.jobs, W.ld, ppj_blk, W.mismatch));
   BT_LAUNCH(k_block_apply<<<gc, T, 0, s>>>(g, W.job_of, W.mismatch, W.susp, W.exlo, W.ld, ctx.st));
