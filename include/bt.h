@@ -76,7 +76,10 @@ typedef struct {
  * BT_FLAG_TINY_QUEUE caps the anchored scan's queue of proposed windows at 64
  * entries, so that nearly every level takes the overflow path, a second scan
  * that tests the windows in place (a test hook; the same tree again). */
-enum { BT_FLAG_DENSE_SCAN = 1, BT_FLAG_TINY_QUEUE = 2 };
+/* BT_FLAG_GRAM_LIST builds the selected-gram list (the gram positions and
+ * hashes the anchored scan shares between levels) whatever the text length;
+ * by default only texts of 8 MiB or more use it (a test hook; same tree). */
+enum { BT_FLAG_DENSE_SCAN = 1, BT_FLAG_TINY_QUEUE = 2, BT_FLAG_GRAM_LIST = 4 };
 
 void bt_opts_default(bt_opts* opts);
 

@@ -21,6 +21,7 @@ BT_OK, BT_EINVAL, BT_ERANGE, BT_ENOMEM, BT_ECUDA, BT_ETIMEOUT, BT_EINTERNAL = ra
 BT_Q_ACCESS, BT_Q_RANK, BT_Q_SELECT = 0, 1, 2
 BT_FLAG_DENSE_SCAN = 1
 BT_FLAG_TINY_QUEUE = 2
+BT_FLAG_GRAM_LIST = 4
 ST_FIELDS = 10
 ST_NAMES = ("nblocks", "b", "cov", "nmarked", "npairs", "verify_bytes", "collisions",
             "final_blocks", "candidates", "hits")
@@ -281,6 +282,7 @@ class BuildOptions:
     max_rounds: int = 0
     dense_scan: bool = False
     tiny_queue: bool = False  # test hook: forces the scan's queue-overflow path
+    gram_list: bool = False  # test hook: selected-gram list whatever the text length
 
     def to_c(self):
         o = bt_opts_default()
@@ -289,8 +291,9 @@ class BuildOptions:
         o.seed = self.seed
         o.modulus = self.modulus
         o.max_rounds = self.max_rounds
-        o.flags = (BT_FLAG_DENSE_SCAN if self.dense_scan else 0) | (
-            BT_FLAG_TINY_QUEUE if self.tiny_queue else 0)
+        o.flags = ((BT_FLAG_DENSE_SCAN if self.dense_scan else 0)
+                   | (BT_FLAG_TINY_QUEUE if self.tiny_queue else 0)
+                   | (BT_FLAG_GRAM_LIST if self.gram_list else 0))
         keep = None
         if self.level_sizes is not None:
             keep = np.ascontiguousarray(self.level_sizes, dtype=np.uint64)

@@ -652,8 +652,11 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_anchor(ScanCtx<M> C0, 
                                                              uint32_t amask,
                                                              const uint32_t* __restrict__ bitmap_g,
                                                              uint32_t bm_smem_words,
-                                                             const uint32_t* __restrict__ secbits_g) {
+                                                             const uint32_t* __restrict__ secbits_g,
+                                                             int sec_only) {
   if (INLINE && C0.ld->qover == 0) return;
+  // sec_only: k_scan_list covers this level unless it has keys without an anchor.
+  if (!INLINE && sec_only && C0.ld->anchorless != 1u && C0.ld->tail_anchorless != 2u) return;
   extern __shared__ uint32_t smem[];
   __shared__ unsigned int s_qn;  // hits this CTA recorded
   uint32_t* sec = smem;                                      // kSecBits / 32 words
@@ -879,6 +882,157 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_anchor(ScanCtx<M> C0, 
   }
 }
 #undef BT_RECORD
+
+// ---------------------------------------------------------------------------
+// The selected-gram list.  On the levels whose block length is a multiple of
+// 128 and whose selection is the default (w = 16, density 1/8), the selected
+// grams of a chunk are the same at every level: their positions and mixed
+// hashes are computed once per build, in 128-byte text chunks (positions of
+// chunk j at gl_chunk[j] .. gl_chunk[j+1] of gl_mx / gl_pos), and those levels
+// read the list instead of rolling the hash again.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kGlSbits = 3;
+constexpr uint64_t kGlMinText = 8ull << 20;  // smaller texts roll the hash at every level
+
+// One 128-byte chunk per thread: count the selected grams starting in it
+// into cnt[j] (WRITE = false), or write them from offset cnt[j] on (WRITE =
+// true, cnt holding the exclusive prefix sums of the counts).
+template <bool WRITE>
+__global__ void __launch_bounds__(256) k_gl_pass(const uint8_t* __restrict__ T, uint64_t n, uint64_t nchunks,
+                                                 uint32_t rb, uint32_t rw, uint32_t sel_max,
+                                                 uint32_t* __restrict__ cnt, uint32_t* __restrict__ out_mx,
+                                                 uint8_t* __restrict__ out_pos) {
+  __shared__ uint32_t slots[256 * kSlotWords];
+  uint32_t* slotw = slots + threadIdx.x * kSlotWords;
+  const bool aligned16 = (((uintptr_t)T) & 15) == 0;
+  const uint64_t xlim = n - 15;  // grams start below n - 15
+  for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < nchunks;
+       j += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t p0 = j * kAnchorQ;
+    const uint32_t nx = (uint32_t)(xlim - p0 < kAnchorQ ? xlim - p0 : kAnchorQ);
+    stage((uint8_t*)slotw, T, n, p0, nx + 15, aligned16);
+    const uint64_t o = WRITE ? cnt[j] : 0;
+    uint32_t c = 0;
+    uint32_t gh = 0;
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+      const uint32_t v = slotw[t];
+#pragma unroll
+      for (int u = 0; u < 4; u++) gh = gh * rb + __byte_perm(v, 0, 0x4440 + u);
+    }
+    {
+      const uint32_t mx = gram_mix(gh);
+      if (mx <= sel_max) {
+        if (WRITE) {
+          out_mx[o] = mx;
+          out_pos[o] = 0;
+        }
+        c++;
+      }
+    }
+#pragma unroll 1
+    for (uint32_t G = 0; G < 4 && 32 * G + 1 < nx; G++) {
+#pragma unroll
+      for (uint32_t qq = 0; qq < 8; qq++) {
+        const uint32_t wo = slotw[8 * G + qq], wn = slotw[8 * G + qq + 4];
+#pragma unroll
+        for (uint32_t u = 0; u < 4; u++) {
+          const uint32_t i = 32 * G + 4 * qq + u + 1;
+          gh = gh * rb + __byte_perm(wn, 0, 0x4440 + u) - __byte_perm(wo, 0, 0x4440 + u) * rw;
+          const uint32_t mx = gram_mix(gh);
+          if (mx <= sel_max && i < nx) {
+            if (WRITE) {
+              out_mx[o + c] = mx;
+              out_pos[o + c] = (uint8_t)i;
+            }
+            c++;
+          }
+        }
+      }
+    }
+    if (!WRITE) cnt[j] = c;
+  }
+}
+
+// The anchored scan of a level from the selected-gram list: per chunk, the
+// listed grams below the chunk's end pass the bitmap filter (four loads in
+// flight) and go to the hit queue.  Levels with keys without an anchor are
+// left to k_scan_anchor (it needs every position's gram).
+template <class M>
+__global__ void __launch_bounds__(256) k_scan_list(ScanCtx<M> C0, GramP gp, uint64_t cpb,
+                                                   const uint32_t* __restrict__ bitmap_g, uint32_t bm_smem_words,
+                                                   const uint32_t* __restrict__ gl_chunk,
+                                                   const uint32_t* __restrict__ gl_mx,
+                                                   const uint8_t* __restrict__ gl_pos) {
+  if (C0.ld->anchorless == 1u || C0.ld->tail_anchorless == 2u) return;
+  extern __shared__ uint32_t bms[];
+  __shared__ unsigned int s_qn;
+  const ScanCtx<M>& C = C0;
+  const Geo& g = C.g;
+  const uint32_t tail_a = C.ld->tail_a;
+  const uint32_t far_end = C.ld->far_end;
+  const uint32_t Wx = gp.W > far_end ? gp.W : far_end;
+  const uint32_t Wt0 = gp.Wr ? gp.Wr : 1;
+  const uint32_t Wt = tail_a != 0xFFFFFFFFu && tail_a + 1 > Wt0 ? tail_a + 1 : Wt0;
+  for (uint32_t i = threadIdx.x; i < bm_smem_words; i += blockDim.x) bms[i] = bitmap_g[i];
+  if (threadIdx.x == 0) s_qn = 0;
+  __syncthreads();
+  const uint32_t* bitmap = bm_smem_words ? bms : bitmap_g;
+  const uint32_t w = gp.w;
+  const uint64_t total = g.c * cpb;
+  const unsigned lane = threadIdx.x & 31;
+  for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x + (threadIdx.x & ~31u); base < total;
+       base += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t wi = base + lane;
+    do {
+      if (wi >= total) break;
+      const uint64_t k = cpb == 1 ? wi : wi / cpb, j = wi - k * cpb;
+      const uint64_t s = g.st[k], len = blen(g, k);
+      const uint64_t p0 = s + j * kAnchorQ;
+      if (p0 >= s + len) break;
+      const uint64_t av = avail_end(g, k);
+      uint64_t xe = p0 + kAnchorQ < s + len ? p0 + kAnchorQ : s + len;
+      uint64_t xm = av >= g.b ? av - g.b + Wx : 0;
+      if (g.r && av >= g.r) {
+        const uint64_t xr = av - g.r + Wt;
+        if (xr > xm) xm = xr;
+      }
+      const uint64_t gram_end = av + 1 >= w ? av + 1 - w : 0;
+      if (xm > gram_end) xm = gram_end;
+      if (xe > xm) xe = xm;
+      if (xe <= p0) break;
+      const uint32_t nx = (uint32_t)(xe - p0);
+      const uint64_t cj = p0 / kAnchorQ;
+      const uint32_t e1 = gl_chunk[cj + 1];
+      for (uint32_t e = gl_chunk[cj]; e < e1; e += 4) {
+        uint32_t pos[4], mx[4], wv[4], bt[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          pos[u] = kAnchorQ;
+          wv[u] = 0;
+          bt[u] = 0;
+          mx[u] = 0;
+          if (e + u < e1) {
+            pos[u] = gl_pos[e + u];
+            mx[u] = gl_mx[e + u];
+            const uint32_t bit = gram_bit(gp, mx[u]);
+            bt[u] = bit & 31;
+            wv[u] = bitmap[bit >> 5];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+          if (pos[u] < nx && ((wv[u] >> bt[u]) & 1u)) record_hit(C, &s_qn, p0 + pos[u], k, mx[u]);
+      }
+    } while (0);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    C.segn[blockIdx.x] = s_qn;
+    atomicAdd(C.qn, (unsigned long long)s_qn);
+    if (s_qn > C.seg) C.ld->qover = 1u;
+  }
+}
 
 // The hits of scan CTA j's segment, one per thread: anchor-table lookup; the
 // windows the anchors propose go to this CTA's candidate segment.
@@ -1638,13 +1792,20 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
     if (rc_a == BT_OK) rc_a = allow_scan_smem<k_scan_anchor<M, true>>(smem_max);
     if (rc_a != BT_OK) return rc_a;
     ProfScope ps("window_scan", s, cov_l);
+    // The selected-gram list serves levels with the default selection whose
+    // chunks are the list's chunks; k_scan_anchor then runs only when the
+    // level has keys without an anchor.
+    const bool use_list = ctx.gl_chunk && gq.w == 16 && gq.sbits == kGlSbits && b % kAnchorQ == 0;
+    if (use_list)
+      BT_LAUNCH(k_scan_list<M><<<scan_grid, kScanThreads, (size_t)bm_smem * 4, s>>>(
+          C, gq, cpa, bitmap, bm_smem, ctx.gl_chunk, ctx.gl_mx, ctx.gl_pos));
     BT_LAUNCH(k_scan_anchor<M, false><<<scan_grid, kScanThreads, smem, s>>>(
-        C, gq, cpa, atab, (uint32_t)(acap - 1), bitmap, bm_smem, secbits));
+        C, gq, cpa, atab, (uint32_t)(acap - 1), bitmap, bm_smem, secbits, use_list ? 1 : 0));
     BT_LAUNCH(k_hits<M><<<scan_grid, 512, 0, s>>>(C, atab, (uint32_t)(acap - 1)));
     BT_LAUNCH(k_candidates<M><<<scan_grid, 256, 0, s>>>(C));
     // Only when the queue overflowed: the scan again, testing windows inline.
     BT_LAUNCH(k_scan_anchor<M, true><<<scan_grid, kScanThreads, smem, s>>>(
-        C, gq, cpa, atab, (uint32_t)(acap - 1), bitmap, bm_smem, secbits));
+        C, gq, cpa, atab, (uint32_t)(acap - 1), bitmap, bm_smem, secbits, 0));
     if (r)
       BT_LAUNCH(k_scan<M><<<grid_for(c * cpb, T), T, 0, s>>>(m, g, cpb, W.bt, bcap - 1, W.pt, pcap - 1,
                                                               W.ld, 1));
@@ -1727,6 +1888,49 @@ int all_levels(const M& m, BuildCtx& ctx) {
   BT_LAUNCH(k_level_start<<<grid_for(r.c, 256), 256, 0, ctx.s>>>(r.c, r.b, r.st));
   uint64_t last_start = (r.c - 1) * r.b;
   const bool trace = getenv("BT_TRACE") != nullptr;
+  // The selected-gram list pays off when several levels cover large texts.
+  struct ListMem {
+    cudaStream_t s;
+    std::vector<void*> p;
+    ~ListMem() {
+      for (void* q : p) cudaFreeAsync(q, s);
+    }
+  } lm{ctx.s, {}};
+  if (!ctx.dense_scan && t->n >= 16 && (t->n >= kGlMinText || ctx.force_list)) {
+    const uint64_t n = t->n, nchunks = (n - 15 + kAnchorQ - 1) / kAnchorQ;
+    uint32_t* chunk;
+    BT_CUDA(cudaMallocAsync((void**)&chunk, (nchunks + 1) * sizeof(uint32_t), ctx.s));
+    lm.p.push_back(chunk);
+    uint32_t *agg, *cnt;
+    BT_CUDA(cudaMallocAsync((void**)&agg, scan_scratch_words(nchunks) * sizeof(uint32_t), ctx.s));
+    lm.p.push_back(agg);
+    BT_CUDA(cudaMallocAsync((void**)&cnt, nchunks * sizeof(uint32_t), ctx.s));
+    lm.p.push_back(cnt);
+    const uint32_t rb = 0x01000193u;
+    uint32_t rw = 1;
+    for (int i = 0; i < 16; i++) rw *= rb;
+    const uint32_t sel_max = (1u << (32 - kGlSbits)) - 1u;
+    const unsigned grid = grid_for(nchunks, 256);
+    {
+      ProfScope ps("gram_list", ctx.s, n);
+      BT_LAUNCH(k_gl_pass<false><<<grid, 256, 0, ctx.s>>>(ctx.T, n, nchunks, rb, rw, sel_max, cnt, nullptr,
+                                                          nullptr));
+      BT_TRY(scan_u32(cnt, chunk, nchunks, ctx.s, agg));
+      uint32_t total = 0;
+      BT_CUDA(cudaMemcpyAsync(&total, chunk + nchunks, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx.s));
+      BT_CUDA(cudaStreamSynchronize(ctx.s));
+      uint32_t* mx;
+      uint8_t* pos;
+      BT_CUDA(cudaMallocAsync((void**)&mx, (uint64_t)(total ? total : 1) * sizeof(uint32_t), ctx.s));
+      lm.p.push_back(mx);
+      BT_CUDA(cudaMallocAsync((void**)&pos, total ? total : 1, ctx.s));
+      lm.p.push_back(pos);
+      BT_LAUNCH(k_gl_pass<true><<<grid, 256, 0, ctx.s>>>(ctx.T, n, nchunks, rb, rw, sel_max, chunk, mx, pos));
+      ctx.gl_chunk = chunk;
+      ctx.gl_mx = mx;
+      ctx.gl_pos = pos;
+    }
+  }
   for (uint32_t l = 0; l < t->L; l++) {
     auto h0 = std::chrono::steady_clock::now();
     BT_TRY(level_pass(m, ctx, l, last_start));
@@ -1737,6 +1941,9 @@ int all_levels(const M& m, BuildCtx& ctx) {
               std::chrono::duration<double, std::milli>(h1 - h0).count());
     }
   }
+  ctx.gl_chunk = nullptr;
+  ctx.gl_mx = nullptr;
+  ctx.gl_pos = nullptr;
   return BT_OK;
 }
 

@@ -217,12 +217,14 @@ def _runs_text(n, seed, alphabet=b"ab", max_run=200):
     return np.frombuffer(bytes(out[:n]), np.uint8)
 
 
-@pytest.mark.parametrize("scan", ["anchored", "dense", "tiny_queue"])
+@pytest.mark.parametrize("scan", ["anchored", "dense", "tiny_queue", "gram_list"])
 def test_anchored_and_dense_scans(scan):
     """Both window-scan strategies give the oracle's tree, including texts whose
     keys have no anchor (long runs) and short tails of every length; so does
-    the anchored scan whose candidate queue overflows at every level."""
-    kw = {"dense_scan": scan == "dense", "tiny_queue": scan == "tiny_queue"}
+    the anchored scan whose candidate queue overflows at every level, and the
+    one that reads the selected-gram list."""
+    kw = {"dense_scan": scan == "dense", "tiny_queue": scan == "tiny_queue",
+          "gram_list": scan == "gram_list"}
     cases = [
         (_runs_text(50_000, 1), 2, 8), (_runs_text(120_001, 2, b"abc", 500), 4, 16),
         (_runs_text(30_000, 3, b"a", 2), 2, 4), (np.full(100_003, 65, np.uint8), 4, 32),
