@@ -68,6 +68,7 @@ struct LevelDev {
   unsigned long long cands;         // windows proposed by anchors and filters
   unsigned long long hits;          // proposed windows whose fingerprint is a key's
   unsigned int qover;               // some CTA's queue segment overflowed
+  unsigned int nfar;                // FarNodes taken
 };
 
 struct Geo {
@@ -305,11 +306,20 @@ struct GramP {
 };
 
 // gram -> offsets at which keys anchor on it.
-struct AnchorSet {
+struct __align__(32) AnchorSet {
   uint32_t gram;             // remapped mixed gram hash (kEmptyGram: empty slot)
   uint32_t far;              // one anchor offset >= W (kNoFar: none)
   unsigned long long offs;   // bit a: some key has its anchor at offset a < W
   unsigned long long maxst;  // largest start of a key anchored on this gram
+  uint32_t more;             // further anchor offsets >= W: a list of FarNodes (kNoFar: none)
+  uint32_t pad;
+};
+
+// A further far anchor offset of a gram (keys whose first selected gram lies
+// beyond the offset mask are rare; two of them on one gram rarer still).
+struct FarNode {
+  uint32_t off;
+  uint32_t next;
 };
 
 // The gram hash is a polynomial in rb over the symbols; its mixed value
@@ -333,8 +343,8 @@ __device__ __forceinline__ uint32_t sec_bit(uint32_t mx) { return (mx * 0x2545F4
 
 // Register the anchor of every key (every block and the tail).
 __global__ void k_anchor_keys(Geo g, GramP gp, const uint32_t* __restrict__ slotB, AnchorSet* atab,
-                              uint32_t amask, uint32_t* bitmap, uint32_t* secbits, LevelDev* ld,
-                              Status* status) {
+                              uint32_t amask, FarNode* fnode, uint32_t fcap, uint32_t* bitmap,
+                              uint32_t* secbits, LevelDev* ld, Status* status) {
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < g.c;
        k += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t s = g.st[k], len = blen(g, k);
@@ -378,8 +388,16 @@ __global__ void k_anchor_keys(Geo g, GramP gp, const uint32_t* __restrict__ slot
             atomicOr(&atab[h].offs, 1ull << a);
           } else {
             const uint32_t f = atomicCAS(&atab[h].far, kNoFar, a);
-            if (f != kNoFar && f != a) sec = true;  // another far offset holds the entry
-            else atomicMax(&ld->far_end, a + 1);
+            if (f != kNoFar && f != a) {  // another far offset holds the entry: a list node
+              const uint32_t id = atomicAdd(&ld->nfar, 1u);
+              if (id < fcap) {
+                fnode[id].off = a;
+                fnode[id].next = atomicExch(&atab[h].more, id);
+              } else {
+                sec = true;
+              }
+            }
+            if (!sec) atomicMax(&ld->far_end, a + 1);
           }
           atomicMax(&atab[h].maxst, (unsigned long long)s);
         } else {
@@ -423,6 +441,7 @@ struct ScanCtx {
   uint32_t* csegn;                   // windows proposed by each k_hits CTA (may exceed cseg)
   uint32_t cseg;
   Status* status;                    // device-side invariant checks
+  const FarNode* fnode;              // further far anchor offsets of the anchor table
 };
 
 // A gram position x found by the scan in (a chunk of) block k: a selected
@@ -533,13 +552,14 @@ __device__ __forceinline__ void anchor_hit(const ScanCtx<M>& C, unsigned int* sq
                                            uint32_t& nhit) {
   const uint32_t gk = gram_key(mx);
   unsigned long long offs = 0, maxst = 0;
-  uint32_t far = kNoFar;
+  uint32_t far = kNoFar, node = kNoFar;
   for (uint32_t h = gram_slot(gk, amask), it = 0; it <= amask; h = (h + 1) & amask, it++) {
     const uint32_t eg = atab[h].gram;
     if (eg == gk) {
       offs = atab[h].offs;
       far = atab[h].far;
       maxst = atab[h].maxst;
+      node = atab[h].more;
       break;
     }
     if (eg == kEmptyGram) break;
@@ -548,25 +568,25 @@ __device__ __forceinline__ void anchor_hit(const ScanCtx<M>& C, unsigned int* sq
   // the leftmost occurrence of any of them, nor of a pair that starts with
   // one of them (both are at or before the key's start).
   bool pt = gk == tail_gram && x >= tail_a;
-  bool pf = far != kNoFar && far <= x && x - far <= maxst;
-  while (offs || pf || pt) {
-    uint64_t p = 0;
-    uint32_t kind = 0;
-    bool ok = true;
+  bool pf = far != kNoFar;
+  while (offs || pf || pt || node != kNoFar) {
+    uint32_t a = 0, kind = 0;
     if (pt) {
       pt = false;
-      p = x - tail_a;
+      a = tail_a;
       kind = 1;
     } else if (offs) {
-      const uint32_t a = __ffsll(offs) - 1;
+      a = __ffsll(offs) - 1;
       offs &= offs - 1;
-      ok = a <= x && x - a <= maxst;
-      p = x - a;
-    } else {
+    } else if (pf) {
       pf = false;
-      p = x - far;
+      a = far;
+    } else {
+      const FarNode fn = C.fnode[node];
+      node = fn.next;
+      a = fn.off;
     }
-    if (ok) propose(C, sq, k, s, av, p, kind, ncand, nhit);
+    if (a <= x && (kind || x - a <= maxst)) propose(C, sq, k, s, av, x - a, kind, ncand, nhit);
   }
 }
 
@@ -1229,11 +1249,57 @@ __global__ void k_pair_jobs(Geo g, const uint32_t* __restrict__ slotP,
 
 // 4b. Byte verification of the queued jobs, in pieces of kPiece bytes, one
 // warp per piece.
-__global__ void __launch_bounds__(256) k_verify(const uint8_t* __restrict__ T, const Job* __restrict__ jobs,
-                                                const LevelDev* ld, uint64_t ppj,
-                                                unsigned int* mismatch) {
+// The 16 bytes T[A, A+16) from the aligned units at A & ~15 (u0, u1).
+__device__ __forceinline__ uint4 unaligned16(uint4 u0, uint4 u1, uint32_t d) {
+  const uint32_t q = d >> 2, sh = 8 * (d & 3);
+  const uint32_t w0 = q == 0 ? u0.x : q == 1 ? u0.y : q == 2 ? u0.z : u0.w;
+  const uint32_t w1 = q == 0 ? u0.y : q == 1 ? u0.z : q == 2 ? u0.w : u1.x;
+  const uint32_t w2 = q == 0 ? u0.z : q == 1 ? u0.w : q == 2 ? u1.x : u1.y;
+  const uint32_t w3 = q == 0 ? u0.w : q == 1 ? u1.x : q == 2 ? u1.y : u1.z;
+  const uint32_t w4 = q == 0 ? u1.x : q == 1 ? u1.y : q == 2 ? u1.z : u1.w;
+  return make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh), __funnelshift_r(w2, w3, sh),
+                    __funnelshift_r(w3, w4, sh));
+}
+
+// Compare T[J.a + x] and T[J.b + x] for x in [off, end): 16 bytes per lane
+// and step when the own side J.b + off is 16-byte aligned (block starts are
+// multiples of 16 at the usual leaf lengths), the other side realigned from
+// two aligned loads; bytes otherwise and for the ragged end.
+__device__ __forceinline__ bool differs(const uint8_t* __restrict__ T, uint64_t n, bool aligned16, uint64_t a,
+                                        uint64_t b, uint64_t off, uint64_t end, unsigned lane) {
+  bool diff = false;
+  uint64_t x = off;
+  if (aligned16 && ((b + off) & 15) == 0) {
+    const uint64_t full = off + ((end - off) & ~15ull);
+    for (uint64_t y = off + 16ull * lane; y < full; y += 512) {
+      const uint4 vb = *(const uint4*)(T + b + y);
+      const uint64_t A = a + y, A0 = A & ~15ull;
+      const uint32_t d = (uint32_t)(A & 15);
+      const uint4 u0 = *(const uint4*)(T + A0);
+      uint4 va;
+      if (d == 0) {
+        va = u0;
+      } else if (A0 + 32 <= n) {
+        va = unaligned16(u0, *(const uint4*)(T + A0 + 16), d);
+      } else {  // the unit past the text's end is not read
+        uint32_t v[4] = {0, 0, 0, 0};
+        for (uint32_t t = 0; t < 16; t++) v[t >> 2] |= (uint32_t)T[A + t] << (8 * (t & 3));
+        va = make_uint4(v[0], v[1], v[2], v[3]);
+      }
+      diff |= va.x != vb.x || va.y != vb.y || va.z != vb.z || va.w != vb.w;
+    }
+    x = full;
+  }
+  for (x += lane; x < end; x += 32) diff |= T[a + x] != T[b + x];
+  return diff;
+}
+
+__global__ void __launch_bounds__(256) k_verify(const uint8_t* __restrict__ T, uint64_t n,
+                                                const Job* __restrict__ jobs, const LevelDev* ld,
+                                                uint64_t ppj, unsigned int* mismatch) {
   const uint64_t njobs = ld->njobs;
   const unsigned lane = threadIdx.x & 31;
+  const bool aligned16 = (((uintptr_t)T) & 15) == 0;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
   for (uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; w < njobs * ppj;
        w += warps) {
@@ -1241,10 +1307,10 @@ __global__ void __launch_bounds__(256) k_verify(const uint8_t* __restrict__ T, c
     const Job J = jobs[jb];
     const uint64_t off = piece * kPiece;
     if (off >= J.len) continue;
-    if (*(volatile unsigned int*)&mismatch[jb]) continue;
+    // Another piece of the job already differed (every lane takes the same branch).
+    if (__any_sync(0xFFFFFFFFu, *(volatile unsigned int*)&mismatch[jb] != 0)) continue;
     const uint64_t end = off + kPiece < J.len ? off + kPiece : J.len;
-    bool diff = false;
-    for (uint64_t x = off + lane; x < end; x += 32) diff |= T[J.a + x] != T[J.b + x];
+    const bool diff = differs(T, n, aligned16, J.a, J.b, off, end, lane);
     if (__any_sync(0xFFFFFFFFu, diff) && lane == 0) atomicOr(&mismatch[jb], 1u);
   }
 }
@@ -1513,6 +1579,7 @@ __global__ void k_level_init(InitArgs a) {
     if (a.atab && i < a.acap) {
       a.atab[i].gram = kEmptyGram;
       a.atab[i].far = kNoFar;
+      a.atab[i].more = kNoFar;
       a.atab[i].offs = 0;
       a.atab[i].maxst = 0;
     }
@@ -1533,6 +1600,7 @@ __global__ void k_level_init(InitArgs a) {
       d.tail_a = 0xFFFFFFFFu;
       d.far_end = 0;
       d.qover = 0;
+      d.nfar = 0;
       d.cands = 0;
       d.hits = 0;
       *a.ld = d;
@@ -1712,6 +1780,8 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
   Arena& A = ctx.arena;
   LevelWork W;
   AnchorSet* atab = nullptr;
+  FarNode* fnode = nullptr;
+  const uint32_t fcap = (uint32_t)(c / 16 + 1024);
   uint32_t *bitmap = nullptr, *secbits = nullptr, *sagg = nullptr;
   Hit* q = nullptr;
   uint32_t* segn = nullptr;
@@ -1736,6 +1806,7 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
     sagg = A.take<uint32_t>(scan_scratch_words(words));
     if (anchored) {
       atab = A.take<AnchorSet>(acap);
+      fnode = A.take<FarNode>(fcap);
       bitmap = A.take<uint32_t>(bwords);
       secbits = A.take<uint32_t>(kSecBits / 32);
       q = A.take<Hit>((uint64_t)seg * scan_grid);
@@ -1780,10 +1851,10 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
     BT_LAUNCH(k_scan<M><<<grid_for(c * cpb, T), T, 0, s>>>(m, g, cpb, W.bt, bcap - 1, W.pt, pcap - 1,
                                                             W.ld, 0));
   } else {
-    BT_LAUNCH(k_anchor_keys<<<gc, T, 0, s>>>(g, gq, W.slotB, atab, (uint32_t)(acap - 1), bitmap, secbits,
+    BT_LAUNCH(k_anchor_keys<<<gc, T, 0, s>>>(g, gq, W.slotB, atab, (uint32_t)(acap - 1), fnode, fcap, bitmap, secbits,
                                              W.ld, ctx.st));
     ScanCtx<M> C{m, g, W.bt, bcap - 1, W.pt, pcap - 1, W.ld, 0, 0,
-                 q, segn, seg, qn, cq, csegn, seg, ctx.st};
+                 q, segn, seg, qn, cq, csegn, seg, ctx.st, fnode};
     const size_t smem_base = ((size_t)kSecBits / 32 + (size_t)kRing * kScanThreads +
                               (size_t)kScanThreads * kSlotWords) * 4;
     const size_t smem = smem_base + (size_t)bm_smem * 4;
@@ -1815,7 +1886,7 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
   // Pairs: verify, resolve collisions exactly, mark.
   const uint64_t ppj_pair = (2 * b + kPiece - 1) / kPiece;
   BT_LAUNCH(k_pair_jobs<<<gc, T, 0, s>>>(g, W.slotP, W.pt, W.plo_k, W.pm, W.jobs, W.job_of, W.ld, ctx.st));
-  BT_LAUNCH(k_verify<<<grid_for(c * ppj_pair * 32, T), T, 0, s>>>(ctx.T, W.jobs, W.ld, ppj_pair, W.mismatch));
+  BT_LAUNCH(k_verify<<<grid_for(c * ppj_pair * 32, T), T, 0, s>>>(ctx.T, n, W.jobs, W.ld, ppj_pair, W.mismatch));
   BT_LAUNCH(k_pair_apply<<<gc, T, 0, s>>>(g, W.job_of, W.mismatch, W.susp, W.exlo, W.ld, ctx.st));
   BT_TRY(exact_pass(m, g, cpb, 1, W, s));
   BT_LAUNCH(k_pair_exact_apply<<<gc, T, 0, s>>>(g, W.susp, W.exlo, W.pm, W.plo_k, W.ld));
@@ -1828,7 +1899,7 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
   const uint64_t ppj_blk = (b + kPiece - 1) / kPiece;
   BT_LAUNCH(k_block_jobs<<<gc, T, 0, s>>>(g, W.slotB, W.bt, v.mw, t->prune, v.lo, W.jobs, W.job_of, W.ld,
                                 ctx.st));
-  BT_LAUNCH(k_verify<<<grid_for(c * ppj_blk * 32, T), T, 0, s>>>(ctx.T, W.jobs, W.ld, ppj_blk, W.mismatch));
+  BT_LAUNCH(k_verify<<<grid_for(c * ppj_blk * 32, T), T, 0, s>>>(ctx.T, n, W.jobs, W.ld, ppj_blk, W.mismatch));
   BT_LAUNCH(k_block_apply<<<gc, T, 0, s>>>(g, W.job_of, W.mismatch, W.susp, W.exlo, W.ld, ctx.st));
   BT_TRY(exact_pass(m, g, cpb, 0, W, s));
   BT_LAUNCH(k_block_exact_apply<<<gc, T, 0, s>>>(W.susp, W.exlo, v.lo, W.ld));

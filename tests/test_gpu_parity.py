@@ -217,6 +217,30 @@ def _runs_text(n, seed, alphabet=b"ab", max_run=200):
     return np.frombuffer(bytes(out[:n]), np.uint8)
 
 
+def _gram_selected(gram: bytes) -> bool:
+    """Whether the anchored scan selects this 16-gram at density 1/8 (its
+    polynomial hash times an odd constant, mod 2^32, below 2^29)."""
+    h = 0
+    for c in gram:
+        h = (h * 0x01000193 + c) & 0xFFFFFFFF
+    return ((h * 0x9E3779B1) & 0xFFFFFFFF) < (1 << 29)
+
+
+def _far_anchor_text(n, seed):
+    """Runs of one byte (whose 16-gram is not selected) of 70-150 bytes, each
+    followed by one of three fixed strings: blocks that start in a run have
+    their first selected gram beyond the 64 offsets of the anchor mask, and
+    blocks with the same string after runs of different lengths anchor on the
+    same gram at different far offsets."""
+    rng = np.random.default_rng(seed)
+    run = next(c for c in b"zyxwvutsrq" if not _gram_selected(bytes([c]) * 16))
+    tails = [bytes(rng.integers(97, 123, 200, dtype=np.uint8)) for _ in range(3)]
+    out = bytearray()
+    while len(out) < n:
+        out += bytes([run]) * int(rng.integers(70, 151)) + tails[int(rng.integers(3))]
+    return np.frombuffer(bytes(out[:n]), np.uint8)
+
+
 @pytest.mark.parametrize("scan", ["anchored", "dense", "tiny_queue", "gram_list"])
 def test_anchored_and_dense_scans(scan):
     """Both window-scan strategies give the oracle's tree, including texts whose
@@ -232,6 +256,7 @@ def test_anchored_and_dense_scans(scan):
         (workloads.text_versions(n=333_333, base_len=20_000, sigma=96, seed=2), 4, 32),
         (workloads.text_versions(n=99_999, base_len=4096, sigma=4, seed=3), 2, 1),
         (workloads.random_bytes(70_001, 3, 4), 3, 2),
+        (_far_anchor_text(200_000, 5), 2, 128), (_far_anchor_text(150_001, 6), 4, 96),
     ]
     for T, tau, leaf in cases:
         for prune in (True, False):
