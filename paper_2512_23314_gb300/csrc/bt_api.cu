@@ -235,7 +235,7 @@ static int build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, 
   uint64_t bytes = t->leaf_bytes + 16 + sizeof(TreeView) + 512 + (t->lv[0].c + 1) * t->S * 8;
   for (const Level& v : t->lv) {
     const uint64_t words = (v.c + 31) / 32;
-    bytes += v.c * (8 + 4 + 8) + (2 * words + 1) * 4 + 2 * v.c * t->S * 4;
+    bytes += v.c * (8 + 4 + 8) + (2 * words + 1) * 4 + 2 * v.c * t->S * v.cw;
   }
   t->dev_bytes = bytes;
   BT_CUDA(cudaStreamSynchronize(s));

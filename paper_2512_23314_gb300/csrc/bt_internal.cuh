@@ -118,8 +118,9 @@ struct Level {
   uint32_t* ptr = nullptr;
   uint64_t* off = nullptr;
   uint64_t* lo = nullptr;  // exact leftmost occurrence of every block (pruning)
-  uint32_t* cnt = nullptr;
-  uint32_t* pc = nullptr;
+  void* cnt = nullptr;     // counter rows, cw bytes per counter
+  void* pc = nullptr;
+  uint32_t cw = 4;
   uint64_t stats[BT_ST_FIELDS] = {};
   std::vector<void*> owned;  // device allocations holding this level's arrays
 };
@@ -133,9 +134,24 @@ struct LevelView {
   const uint32_t* mr;
   const uint32_t* ptr;
   const uint64_t* off;
-  const uint32_t* cnt;
-  const uint32_t* pc;
+  const void* cnt;  // symbol counters of the blocks, cw bytes each (1, 2 or 4)
+  const void* pc;
+  uint32_t cw;
 };
+
+// Bytes per symbol counter of a level with block length b: a count never
+// exceeds b.
+inline uint32_t counter_width(uint64_t b) { return b <= 0xFF ? 1 : b <= 0xFFFF ? 2 : 4; }
+
+// Counter i of a row array with w-byte entries.
+__device__ __forceinline__ uint32_t cget(const void* a, uint32_t w, uint64_t i) {
+  return w == 1 ? ((const uint8_t*)a)[i] : w == 2 ? ((const uint16_t*)a)[i] : ((const uint32_t*)a)[i];
+}
+__device__ __forceinline__ void cput(void* a, uint32_t w, uint64_t i, uint32_t v) {
+  if (w == 1) ((uint8_t*)a)[i] = (uint8_t)v;
+  else if (w == 2) ((uint16_t*)a)[i] = (uint16_t)v;
+  else ((uint32_t*)a)[i] = v;
+}
 
 constexpr int kMaxLevels = 64;
 

@@ -114,11 +114,14 @@ struct __align__(16) PSlot {
 };
 
 // Open addressing with linear probing on the slots' keys.
+// A plain read comes first: repeated keys (the same block content in many
+// versions) find their slot without an atomic on a contended address.
 template <class S>
 __device__ __forceinline__ uint32_t tbl_insert(S* t, uint64_t mask, uint64_t key) {
   uint64_t h = mix64(key) & mask;
   for (uint64_t it = 0; it <= mask; it++) {
-    unsigned long long old = atomicCAS(&t[h].key, (unsigned long long)kNone, (unsigned long long)key);
+    unsigned long long old = *(volatile unsigned long long*)&t[h].key;
+    if (old == kNone) old = atomicCAS(&t[h].key, (unsigned long long)kNone, (unsigned long long)key);
     if (old == kNone || old == key) return (uint32_t)h;
     h = (h + 1) & mask;
   }
@@ -187,14 +190,21 @@ __global__ void k_block_fp(M m, Geo g, uint64_t* __restrict__ fpB, uint32_t* __r
 // 2. Pair-table insertion: key (slot_k, slot_k+1) for pairs of full blocks.
 __global__ void k_pair_insert(Geo g, const uint32_t* __restrict__ slotB, uint32_t* __restrict__ slotP,
                               PSlot* pt, uint64_t pmask, BSlot* bt, LevelDev* ld, Status* status) {
-  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k + 1 < g.c;
-       k += (uint64_t)gridDim.x * blockDim.x) {
+  // Warp-uniform loop: the pair count is summed per warp (one atomic each).
+  const unsigned lane = threadIdx.x & 31;
+  for (uint64_t base = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull; base + 1 < g.c;
+       base += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = base + lane;
+    const bool pair = k + 1 < g.c && g.st[k + 1] == g.st[k] + g.b;
+    const uint32_t np = __popc(__ballot_sync(0xFFFFFFFFu, pair));
+    if (lane == 0 && np) atomicAdd(&ld->npairs, np);
+    if (k + 1 >= g.c) continue;
     uint32_t sp = kNoSlot;
-    if (g.st[k + 1] == g.st[k] + g.b) {
-      atomicAdd(&ld->npairs, 1u);
+    if (pair) {
       // The last pair start per first-block slot: a window after it cannot
       // be the leftmost occurrence of any pair that starts with that slot.
-      if (slotB[k] != kNoSlot) atomicMax(&bt[slotB[k]].maxpst, (unsigned long long)g.st[k]);
+      if (slotB[k] != kNoSlot && *(volatile unsigned long long*)&bt[slotB[k]].maxpst < g.st[k])
+        atomicMax(&bt[slotB[k]].maxpst, (unsigned long long)g.st[k]);
       if (slotB[k + 1] == kNoSlot) {
         sp = kTailPair;
         ld->pretail_slot = slotB[k];

@@ -307,10 +307,12 @@ int prune_tree(BuildCtx& ctx, uint64_t max_rounds) {
   cudaStream_t s = ctx.s;
   const unsigned T = 256;
   if (max_rounds == 0) max_rounds = 4096;
-  const uint32_t multi_rounds = 24;  // multi-CTA rounds before the one-CTA tail
   for (int l = (int)t->L - 2; l >= 0; l--) {
     Level& v = t->lv[l];
     Level& w = t->lv[l + 1];
+    // Multi-CTA rounds before the one-CTA tail; a level of at most 16 Ki
+    // blocks goes to the one-CTA rounds at once (launches cost more there).
+    const uint32_t multi_rounds = v.c <= (16u << 10) ? 0 : 24;
     const int w_last = l + 1 == (int)t->L - 1;
     const uint64_t words = (v.c + 31) / 32;
     Arena& A = ctx.arena;

@@ -50,7 +50,8 @@ struct CountJob {
   const uint64_t* off;
   const uint32_t* mw;
   uint64_t c, b, n;
-  uint32_t* out;        // rows of S counters
+  void* out;            // rows of S counters of cw bytes
+  uint32_t cw;
   int mode;             // 0: count the block itself, 1: count T[st[ptr], st[ptr]+off)
   int only_unmarked;    // skip marked blocks
   int only_marked;
@@ -59,7 +60,9 @@ struct CountJob {
 constexpr uint64_t kCountPiece = 1 << 16;
 
 // One warp per (block, piece of at most 64 KiB); symbol counts are gathered
-// in a per-warp shared histogram and added to the block's row.
+// in a per-warp shared histogram.  Narrow rows (blocks of at most 64 KiB, one
+// piece) are written whole; 4-byte rows (several pieces) are added to with
+// atomics.
 __global__ void __launch_bounds__(256) k_count(CountJob J, const int16_t* __restrict__ sym,
                                                const uint8_t* __restrict__ T, uint32_t S,
                                                uint64_t ppb) {
@@ -80,14 +83,24 @@ __global__ void __launch_bounds__(256) k_count(CountJob J, const int16_t* __rest
       len = J.off[k];
     }
     const uint64_t a = piece * kCountPiece;
-    if (a >= len) continue;
+    if (a >= len) {
+      // An empty range (a pointer at offset 0): narrow rows are not zeroed
+      // beforehand, so the row is written here.
+      if (J.cw < 4 && piece == 0)
+        for (uint32_t i = lane; i < S; i += 32) cput(J.out, J.cw, k * S + i, 0u);
+      continue;
+    }
     const uint64_t e = a + kCountPiece < len ? a + kCountPiece : len;
     for (uint32_t i = lane; i < S; i += 32) h[i] = 0;
     __syncwarp();
     for (uint64_t x = a + lane; x < e; x += 32) atomicAdd(&h[sym[T[s0 + x]]], 1u);
     __syncwarp();
-    for (uint32_t i = lane; i < S; i += 32)
-      if (h[i]) atomicAdd(&J.out[k * S + i], h[i]);
+    if (J.cw < 4) {
+      for (uint32_t i = lane; i < S; i += 32) cput(J.out, J.cw, k * S + i, h[i]);
+    } else {
+      for (uint32_t i = lane; i < S; i += 32)
+        if (h[i]) atomicAdd((uint32_t*)J.out + k * S + i, h[i]);
+    }
     __syncwarp();
   }
 }
@@ -95,8 +108,8 @@ __global__ void __launch_bounds__(256) k_count(CountJob J, const int16_t* __rest
 // Marked blocks of a non-last level: sum of the children's counts.
 __global__ void k_sum_children(uint64_t c, uint64_t b, uint64_t n, const uint64_t* __restrict__ st,
                                const uint32_t* __restrict__ mw, const uint32_t* __restrict__ mr,
-                               uint32_t arity, uint64_t bn, const uint32_t* __restrict__ child_cnt,
-                               uint32_t S, uint32_t* __restrict__ cnt) {
+                               uint32_t arity, uint64_t bn, const void* __restrict__ child_cnt,
+                               uint32_t child_cw, uint32_t S, void* __restrict__ cnt, uint32_t cw) {
   for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < c * S;
        w += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t k = w / S, s = w - k * S;
@@ -105,18 +118,18 @@ __global__ void k_sum_children(uint64_t c, uint64_t b, uint64_t n, const uint64_
     uint64_t first = (mr[k >> 5] + __popc(mw[k >> 5] & ((1u << (k & 31)) - 1u))) * (uint64_t)arity;
     uint64_t nch = (len + bn - 1) / bn;
     uint32_t acc = 0;
-    for (uint64_t i = 0; i < nch; i++) acc += child_cnt[(first + i) * S + s];
-    cnt[k * S + s] = acc;
+    for (uint64_t i = 0; i < nch; i++) acc += cget(child_cnt, child_cw, (first + i) * S + s);
+    cput(cnt, cw, k * S + s, acc);
   }
 }
 
-__global__ void k_level1_prefix(uint64_t c, const uint32_t* __restrict__ cnt, uint32_t S,
+__global__ void k_level1_prefix(uint64_t c, const void* __restrict__ cnt, uint32_t cw, uint32_t S,
                                 uint64_t* __restrict__ pre) {
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
     uint64_t acc = 0;
     for (uint64_t k = 0; k < c; k++) {
       pre[k * S + s] = acc;
-      acc += cnt[k * S + s];
+      acc += cget(cnt, cw, k * S + s);
     }
     pre[c * S + s] = acc;
   }
@@ -182,7 +195,7 @@ __device__ uint64_t q_rank(const TreeView& t, uint32_t c, uint64_t i) {
     const LevelView& v = t.lv[l];
     if (o == 0) return (uint64_t)acc;
     uint64_t len = qlen(t, v, k);
-    if (o == len) return (uint64_t)(acc + v.cnt[k * S + s]);
+    if (o == len) return (uint64_t)(acc + cget(v.cnt, v.cw, k * S + s));
     if (qmarked(v, k)) {
       if (l + 1 == t.L) {
         const uint8_t* p = t.leaf + qrank(v, k) * v.b;
@@ -191,19 +204,19 @@ __device__ uint64_t q_rank(const TreeView& t, uint32_t c, uint64_t i) {
       }
       const LevelView& w = t.lv[l + 1];
       uint64_t j = o / w.b, f = qrank(v, k) * v.arity;
-      for (uint64_t x = 0; x < j; x++) acc += w.cnt[(f + x) * S + s];
+      for (uint64_t x = 0; x < j; x++) acc += cget(w.cnt, w.cw, (f + x) * S + s);
       o -= j * w.b;
       k = f + j;
       l++;
     } else {
       uint64_t P = v.ptr[k], x = v.off[k] + o;
-      acc -= v.pc[k * S + s];
+      acc -= cget(v.pc, v.cw, k * S + s);
       uint64_t lp = qlen(t, v, P);
       if (x <= lp) {
         k = P;
         o = x;
       } else {
-        acc += v.cnt[P * S + s];
+        acc += cget(v.cnt, v.cw, P * S + s);
         k = P + 1;
         o = x - lp;
       }
@@ -240,8 +253,8 @@ __device__ uint64_t q_select(const TreeView& t, uint32_t c, uint64_t j) {
       }
       const LevelView& w = t.lv[l + 1];
       uint64_t f = qrank(v, k) * v.arity, i = 0;
-      while (i < v.arity && w.cnt[(f + i) * S + s] < j) {
-        j -= w.cnt[(f + i) * S + s];
+      while (i < v.arity && cget(w.cnt, w.cw, (f + i) * S + s) < j) {
+        j -= cget(w.cnt, w.cw, (f + i) * S + s);
         i++;
       }
       if (i == v.arity) return kNone;
@@ -249,14 +262,15 @@ __device__ uint64_t q_select(const TreeView& t, uint32_t c, uint64_t j) {
       k = f + i;
       l++;
     } else {
-      uint64_t P = v.ptr[k], jj = j + v.pc[k * S + s];
-      if (jj <= v.cnt[P * S + s]) {
+      uint64_t P = v.ptr[k], jj = j + cget(v.pc, v.cw, k * S + s);
+      const uint32_t cp = cget(v.cnt, v.cw, P * S + s);
+      if (jj <= cp) {
         res -= (int64_t)v.off[k];
         k = P;
         j = jj;
       } else {
         res += (int64_t)(qlen(t, v, P) - v.off[k]);
-        j = jj - v.cnt[P * S + s];
+        j = jj - cp;
         k = P + 1;
       }
     }
@@ -306,30 +320,33 @@ int build_counters(BuildCtx& ctx) {
   const size_t smem = 8 * S * sizeof(unsigned int);
   for (int l = (int)t->L - 1; l >= 0; l--) {
     Level& v = t->lv[l];
-    const uint64_t half = ((v.c * S * sizeof(uint32_t) + 4) + 255) & ~255ull;
+    // Counters of cw bytes (a count never exceeds b).  Narrow rows are
+    // written whole by the kernels; 4-byte rows are accumulated from zero.
+    v.cw = counter_width(v.b);
+    const uint64_t half = ((v.c * S * v.cw + 4) + 255) & ~255ull;
     char* mem;
     BT_CUDA(cudaMallocAsync((void**)&mem, 2 * half, s));
     v.owned.push_back(mem);
-    v.cnt = (uint32_t*)mem;
-    v.pc = (uint32_t*)(mem + half);
-    BT_CUDA(cudaMemsetAsync(mem, 0, 2 * half, s));
+    v.cnt = mem;
+    v.pc = mem + half;
+    if (v.cw == 4) BT_CUDA(cudaMemsetAsync(mem, 0, 2 * half, s));
     const uint64_t ppb = (v.b + kCountPiece - 1) / kCountPiece;
     const bool last = l + 1 == (int)t->L;
-    CountJob J{v.st, v.ptr, v.off, v.mw, v.c, v.b, t->n, v.cnt, 0, 0, 0};
+    CountJob J{v.st, v.ptr, v.off, v.mw, v.c, v.b, t->n, v.cnt, v.cw, 0, 0, 0};
     if (!last) {
       const Level& w = t->lv[l + 1];
       BT_LAUNCH(k_sum_children<<<grid_for(v.c * S, T), T, 0, s>>>(v.c, v.b, t->n, v.st, v.mw, v.mr, v.arity, w.b,
-                                                        w.cnt, S, v.cnt));
+                                                        w.cnt, w.cw, S, v.cnt, v.cw));
       J.only_unmarked = 1;  // marked blocks are sums of their children
     }
     BT_LAUNCH(k_count<<<grid_for(v.c * ppb * 32, T), T, smem, s>>>(J, t->sym, ctx.T, S, ppb));
-    CountJob P{v.st, v.ptr, v.off, v.mw, v.c, v.b, t->n, v.pc, 1, 1, 0};
+    CountJob P{v.st, v.ptr, v.off, v.mw, v.c, v.b, t->n, v.pc, v.cw, 1, 1, 0};
     BT_LAUNCH(k_count<<<grid_for(v.c * ppb * 32, T), T, smem, s>>>(P, t->sym, ctx.T, S, ppb));
     BT_CUDA(cudaGetLastError());
   }
   const Level& r = t->lv[0];
   BT_CUDA(cudaMallocAsync(&t->pre, (r.c + 1) * S * sizeof(uint64_t) + 8, s));
-  BT_LAUNCH(k_level1_prefix<<<1, 256, 0, s>>>(r.c, r.cnt, S, t->pre));
+  BT_LAUNCH(k_level1_prefix<<<1, 256, 0, s>>>(r.c, r.cnt, r.cw, S, t->pre));
   // Leaf text of the marked last-level blocks.
   const Level& z = t->lv[t->L - 1];
   uint32_t nm = 0;
@@ -361,7 +378,7 @@ int upload_view(bt_tree* t, cudaStream_t s) {
   h.S = t->S;
   for (uint32_t l = 0; l < t->L; l++) {
     const Level& v = t->lv[l];
-    h.lv[l] = LevelView{v.c, v.b, v.arity, v.st, v.mw, v.mr, v.ptr, v.off, v.cnt, v.pc};
+    h.lv[l] = LevelView{v.c, v.b, v.arity, v.st, v.mw, v.mr, v.ptr, v.off, v.cnt, v.pc, v.cw};
   }
   h.pre = t->pre;
   h.leaf = t->leaf;
