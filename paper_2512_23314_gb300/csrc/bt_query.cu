@@ -105,6 +105,54 @@ __global__ void __launch_bounds__(256) k_count(CountJob J, const int16_t* __rest
   }
 }
 
+// Small blocks (one-byte counters, b <= 255): one thread per block counts
+// into a private shared-memory row (16-byte text loads when aligned); the
+// CTA's rows are contiguous in the output and go out with word stores.
+// Rows of blocks that are not counted (J.only_*) are written as zeros; a
+// later kernel may overwrite them.
+constexpr uint32_t kSmallCountThreads = 128;
+
+__global__ void __launch_bounds__(kSmallCountThreads) k_count_small(CountJob J, const int16_t* __restrict__ sym_g,
+                                                                    const uint8_t* __restrict__ T, uint32_t S) {
+  extern __shared__ uint8_t rows[];  // kSmallCountThreads rows of S bytes, then the symbol map
+  int16_t* sym = (int16_t*)(rows + ((kSmallCountThreads * S + 3) & ~3u));
+  for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) sym[i] = sym_g[i];
+  uint8_t* row = rows + threadIdx.x * S;
+  for (uint32_t i = 0; i < S; i++) row[i] = 0;
+  __syncthreads();
+  const uint64_t k0 = (uint64_t)blockIdx.x * kSmallCountThreads, k = k0 + threadIdx.x;
+  if (k < J.c) {
+    const bool mk = (J.mw[k >> 5] >> (k & 31)) & 1u;
+    if (!((J.only_unmarked && mk) || (J.only_marked && !mk))) {
+      uint64_t s0, len;
+      if (J.mode == 0) {
+        s0 = J.st[k];
+        len = J.n - s0 < J.b ? J.n - s0 : J.b;
+      } else {
+        s0 = J.st[J.ptr[k]];
+        len = J.off[k];
+      }
+      uint64_t x = 0;
+      if ((((uintptr_t)(T + s0)) & 15) == 0) {
+        for (; x + 16 <= len; x += 16) {
+          const uint4 v = *(const uint4*)(T + s0 + x);
+          const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int t = 0; t < 16; t++) row[sym[(w[t >> 2] >> (8 * (t & 3))) & 0xFF]]++;
+        }
+      }
+      for (; x < len; x++) row[sym[T[s0 + x]]]++;
+    }
+  }
+  __syncthreads();
+  const uint64_t nrows = J.c - k0 < kSmallCountThreads ? J.c - k0 : kSmallCountThreads;
+  const uint64_t nbytes = nrows * S;
+  uint8_t* out = (uint8_t*)J.out + k0 * S;
+  const uint64_t nwords = ((((uintptr_t)out) & 3) == 0) ? nbytes / 4 : 0;
+  for (uint64_t i = threadIdx.x; i < nwords; i += blockDim.x) ((uint32_t*)out)[i] = ((const uint32_t*)rows)[i];
+  for (uint64_t i = nwords * 4 + threadIdx.x; i < nbytes; i += blockDim.x) out[i] = rows[i];
+}
+
 // Marked blocks of a non-last level: sum of the children's counts.
 __global__ void k_sum_children(uint64_t c, uint64_t b, uint64_t n, const uint64_t* __restrict__ st,
                                const uint32_t* __restrict__ mw, const uint32_t* __restrict__ mr,
@@ -333,15 +381,24 @@ int build_counters(BuildCtx& ctx) {
     const uint64_t ppb = (v.b + kCountPiece - 1) / kCountPiece;
     const bool last = l + 1 == (int)t->L;
     CountJob J{v.st, v.ptr, v.off, v.mw, v.c, v.b, t->n, v.cnt, v.cw, 0, 0, 0};
+    CountJob P{v.st, v.ptr, v.off, v.mw, v.c, v.b, t->n, v.pc, v.cw, 1, 1, 0};
+    if (!last) J.only_unmarked = 1;  // marked blocks are sums of their children
+    if (v.cw == 1) {
+      // One thread per block; the rows of marked blocks are written as zeros
+      // and the sums of children overwrite them below.
+      const size_t sm1 = ((kSmallCountThreads * S + 3) & ~3u) + 256 * sizeof(int16_t);
+      const unsigned g1 = (unsigned)((v.c + kSmallCountThreads - 1) / kSmallCountThreads);
+      BT_LAUNCH(k_count_small<<<g1, kSmallCountThreads, sm1, s>>>(J, t->sym, ctx.T, S));
+      BT_LAUNCH(k_count_small<<<g1, kSmallCountThreads, sm1, s>>>(P, t->sym, ctx.T, S));
+    } else {
+      BT_LAUNCH(k_count<<<grid_for(v.c * ppb * 32, T), T, smem, s>>>(J, t->sym, ctx.T, S, ppb));
+      BT_LAUNCH(k_count<<<grid_for(v.c * ppb * 32, T), T, smem, s>>>(P, t->sym, ctx.T, S, ppb));
+    }
     if (!last) {
       const Level& w = t->lv[l + 1];
       BT_LAUNCH(k_sum_children<<<grid_for(v.c * S, T), T, 0, s>>>(v.c, v.b, t->n, v.st, v.mw, v.mr, v.arity, w.b,
                                                         w.cnt, w.cw, S, v.cnt, v.cw));
-      J.only_unmarked = 1;  // marked blocks are sums of their children
     }
-    BT_LAUNCH(k_count<<<grid_for(v.c * ppb * 32, T), T, smem, s>>>(J, t->sym, ctx.T, S, ppb));
-    CountJob P{v.st, v.ptr, v.off, v.mw, v.c, v.b, t->n, v.pc, v.cw, 1, 1, 0};
-    BT_LAUNCH(k_count<<<grid_for(v.c * ppb * 32, T), T, smem, s>>>(P, t->sym, ctx.T, S, ppb));
     BT_CUDA(cudaGetLastError());
   }
   const Level& r = t->lv[0];
