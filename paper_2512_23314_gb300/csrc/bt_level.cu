@@ -180,9 +180,13 @@ __global__ void k_block_fp(M m, Geo g, uint64_t* __restrict__ fpB, uint32_t* __r
         continue;
       }
       slotB[k] = slot;
+      // A block's own start is an occurrence: the slot minimum starts there
+      // (the scan need not propose own windows).
+      if (*(volatile unsigned long long*)&bt[slot].lo > s) atomicMin(&bt[slot].lo, (unsigned long long)s);
     } else {
       slotB[k] = kNoSlot;
       ld->fp_tail = fp;
+      atomicMin(&ld->lo_tail, (unsigned long long)s);
     }
   }
 }
@@ -208,9 +212,12 @@ __global__ void k_pair_insert(Geo g, const uint32_t* __restrict__ slotB, uint32_
       if (slotB[k + 1] == kNoSlot) {
         sp = kTailPair;
         ld->pretail_slot = slotB[k];
+        atomicMin(&ld->lo_tailpair, (unsigned long long)g.st[k]);  // its own start
       } else {
         sp = tbl_insert(pt, pmask, ((uint64_t)slotB[k] << 32) | slotB[k + 1]);
         if (sp == kNoSlot) atomicExch(&status->error, 2ull);
+        else if (*(volatile unsigned long long*)&pt[sp].lo > g.st[k])
+          atomicMin(&pt[sp].lo, (unsigned long long)g.st[k]);  // its own start
       }
     }
     slotP[k] = sp;
@@ -452,6 +459,7 @@ struct ScanCtx {
   uint32_t cseg;
   Status* status;                    // device-side invariant checks
   const FarNode* fnode;              // further far anchor offsets of the anchor table
+  const uint32_t* slotB;             // block slot of every block
 };
 
 // A gram position x found by the scan in (a chunk of) block k: a selected
@@ -536,6 +544,16 @@ __device__ __forceinline__ void propose(const ScanCtx<M>& C, unsigned int* sq, u
                                         uint32_t& nhit) {
   uint64_t avp;
   if (!window_in_run(C.g, k, s, av, p, kind ? C.g.r : C.g.b, &avp)) return;
+  // Own windows (a full block at its start, the tail at its start) are
+  // occurrences the tables start with; so are the pairs starting there.  A
+  // full block with the slot of the block before the tail is still tested:
+  // the pair ending in the tail may occur at its start.
+  if (kind == 0) {
+    const uint64_t own = (p == s && C.g.n - s >= C.g.b) ? k : (p + C.g.b == s ? k - 1 : kNone);
+    if (own != kNone && !(C.g.r && C.slotB[own] == C.pretail)) return;
+  } else if (p == s && C.g.n - s < C.g.b) {
+    return;
+  }
   if (!sq) {
     test_candidate(C, p, avp, kind, ncand, nhit);
     return;
@@ -1073,6 +1091,7 @@ __global__ void __launch_bounds__(512) k_hits(ScanCtx<M> C0, const AnchorSet* __
   if (threadIdx.x == 0) s_cn = 0;
   __syncthreads();
   ScanCtx<M> C = C0;
+  C.pretail = C.ld->pretail_slot;
   const Geo& g = C.g;
   const bool anchorless = C.ld->anchorless == 1u;
   const bool tail_sec = C.ld->tail_anchorless == 2u;
@@ -1276,12 +1295,12 @@ __device__ __forceinline__ uint4 unaligned16(uint4 u0, uint4 u1, uint32_t d) {
 // multiples of 16 at the usual leaf lengths), the other side realigned from
 // two aligned loads; bytes otherwise and for the ragged end.
 __device__ __forceinline__ bool differs(const uint8_t* __restrict__ T, uint64_t n, bool aligned16, uint64_t a,
-                                        uint64_t b, uint64_t off, uint64_t end, unsigned lane) {
+                                        uint64_t b, uint64_t off, uint64_t end, unsigned lane, unsigned L) {
   bool diff = false;
   uint64_t x = off;
   if (aligned16 && ((b + off) & 15) == 0) {
     const uint64_t full = off + ((end - off) & ~15ull);
-    for (uint64_t y = off + 16ull * lane; y < full; y += 512) {
+    for (uint64_t y = off + 16ull * lane; y < full; y += 16ull * L) {
       const uint4 vb = *(const uint4*)(T + b + y);
       const uint64_t A = a + y, A0 = A & ~15ull;
       const uint32_t d = (uint32_t)(A & 15);
@@ -1300,28 +1319,39 @@ __device__ __forceinline__ bool differs(const uint8_t* __restrict__ T, uint64_t 
     }
     x = full;
   }
-  for (x += lane; x < end; x += 32) diff |= T[a + x] != T[b + x];
+  for (x += lane; x < end; x += L) diff |= T[a + x] != T[b + x];
   return diff;
 }
 
+// One group of L lanes (a power of two up to 32, about b/16 so that short
+// jobs do not leave most of a warp idle) per (job, piece of 4 KiB).
 __global__ void __launch_bounds__(256) k_verify(const uint8_t* __restrict__ T, uint64_t n,
                                                 const Job* __restrict__ jobs, const LevelDev* ld,
-                                                uint64_t ppj, unsigned int* mismatch) {
-  const uint64_t njobs = ld->njobs;
-  const unsigned lane = threadIdx.x & 31;
+                                                uint64_t ppj, unsigned int* mismatch, unsigned L) {
+  const uint64_t total = ld->njobs * ppj;
+  const unsigned lane = threadIdx.x & 31, grp = lane / L, gl = lane % L, gpw = 32 / L;
+  const unsigned gmask = (L == 32 ? 0xFFFFFFFFu : ((1u << L) - 1u)) << (grp * L);
   const bool aligned16 = (((uintptr_t)T) & 15) == 0;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
-  for (uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; w < njobs * ppj;
-       w += warps) {
-    const uint64_t jb = w / ppj, piece = w - jb * ppj;
-    const Job J = jobs[jb];
-    const uint64_t off = piece * kPiece;
-    if (off >= J.len) continue;
-    // Another piece of the job already differed (every lane takes the same branch).
-    if (__any_sync(0xFFFFFFFFu, *(volatile unsigned int*)&mismatch[jb] != 0)) continue;
-    const uint64_t end = off + kPiece < J.len ? off + kPiece : J.len;
-    const bool diff = differs(T, n, aligned16, J.a, J.b, off, end, lane);
-    if (__any_sync(0xFFFFFFFFu, diff) && lane == 0) atomicOr(&mismatch[jb], 1u);
+  // Warp-uniform loop: every lane reaches the ballot of every iteration.
+  for (uint64_t base = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32 * gpw; base < total;
+       base += warps * gpw) {
+    const uint64_t u = base + grp;
+    bool diff = false, active = false;
+    uint64_t jb = 0;
+    if (u < total) {
+      jb = u / ppj;
+      const uint64_t piece = u - jb * ppj;
+      const Job J = jobs[jb];
+      const uint64_t off = piece * kPiece;
+      if (off < J.len && *(volatile unsigned int*)&mismatch[jb] == 0) {
+        active = true;
+        const uint64_t end = off + kPiece < J.len ? off + kPiece : J.len;
+        diff = differs(T, n, aligned16, J.a, J.b, off, end, gl, L);
+      }
+    }
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, diff);
+    if (active && gl == 0 && (bal & gmask)) atomicOr(&mismatch[jb], 1u);
   }
 }
 
@@ -1864,7 +1894,7 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
     BT_LAUNCH(k_anchor_keys<<<gc, T, 0, s>>>(g, gq, W.slotB, atab, (uint32_t)(acap - 1), fnode, fcap, bitmap, secbits,
                                              W.ld, ctx.st));
     ScanCtx<M> C{m, g, W.bt, bcap - 1, W.pt, pcap - 1, W.ld, 0, 0,
-                 q, segn, seg, qn, cq, csegn, seg, ctx.st, fnode};
+                 q, segn, seg, qn, cq, csegn, seg, ctx.st, fnode, W.slotB};
     const size_t smem_base = ((size_t)kSecBits / 32 + (size_t)kRing * kScanThreads +
                               (size_t)kScanThreads * kSlotWords) * 4;
     const size_t smem = smem_base + (size_t)bm_smem * 4;
@@ -1896,7 +1926,9 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
   // Pairs: verify, resolve collisions exactly, mark.
   const uint64_t ppj_pair = (2 * b + kPiece - 1) / kPiece;
   BT_LAUNCH(k_pair_jobs<<<gc, T, 0, s>>>(g, W.slotP, W.pt, W.plo_k, W.pm, W.jobs, W.job_of, W.ld, ctx.st));
-  BT_LAUNCH(k_verify<<<grid_for(c * ppj_pair * 32, T), T, 0, s>>>(ctx.T, n, W.jobs, W.ld, ppj_pair, W.mismatch));
+  const unsigned vl = b >= 512 ? 32u : b >= 256 ? 16u : b >= 128 ? 8u : b >= 64 ? 4u : 2u;  // lanes per job
+  BT_LAUNCH(k_verify<<<grid_for(c * ppj_pair * vl, T), T, 0, s>>>(ctx.T, n, W.jobs, W.ld, ppj_pair, W.mismatch,
+                                                                  vl));
   BT_LAUNCH(k_pair_apply<<<gc, T, 0, s>>>(g, W.job_of, W.mismatch, W.susp, W.exlo, W.ld, ctx.st));
   BT_TRY(exact_pass(m, g, cpb, 1, W, s));
   BT_LAUNCH(k_pair_exact_apply<<<gc, T, 0, s>>>(g, W.susp, W.exlo, W.pm, W.plo_k, W.ld));
@@ -1909,7 +1941,8 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
   const uint64_t ppj_blk = (b + kPiece - 1) / kPiece;
   BT_LAUNCH(k_block_jobs<<<gc, T, 0, s>>>(g, W.slotB, W.bt, v.mw, t->prune, v.lo, W.jobs, W.job_of, W.ld,
                                 ctx.st));
-  BT_LAUNCH(k_verify<<<grid_for(c * ppj_blk * 32, T), T, 0, s>>>(ctx.T, n, W.jobs, W.ld, ppj_blk, W.mismatch));
+  BT_LAUNCH(k_verify<<<grid_for(c * ppj_blk * vl, T), T, 0, s>>>(ctx.T, n, W.jobs, W.ld, ppj_blk, W.mismatch,
+                                                                 vl));
   BT_LAUNCH(k_block_apply<<<gc, T, 0, s>>>(g, W.job_of, W.mismatch, W.susp, W.exlo, W.ld, ctx.st));
   BT_TRY(exact_pass(m, g, cpb, 0, W, s));
   BT_LAUNCH(k_block_exact_apply<<<gc, T, 0, s>>>(W.susp, W.exlo, v.lo, W.ld));

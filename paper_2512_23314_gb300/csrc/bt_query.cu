@@ -153,21 +153,24 @@ __global__ void __launch_bounds__(kSmallCountThreads) k_count_small(CountJob J, 
   for (uint64_t i = nwords * 4 + threadIdx.x; i < nbytes; i += blockDim.x) out[i] = rows[i];
 }
 
-// Marked blocks of a non-last level: sum of the children's counts.
+// Marked blocks of a non-last level: sum of the children's counts, one warp
+// per block (lanes over the symbols).
 __global__ void k_sum_children(uint64_t c, uint64_t b, uint64_t n, const uint64_t* __restrict__ st,
                                const uint32_t* __restrict__ mw, const uint32_t* __restrict__ mr,
                                uint32_t arity, uint64_t bn, const void* __restrict__ child_cnt,
                                uint32_t child_cw, uint32_t S, void* __restrict__ cnt, uint32_t cw) {
-  for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < c * S;
-       w += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t k = w / S, s = w - k * S;
+  const unsigned lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+  for (uint64_t k = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; k < c; k += warps) {
     if (!((mw[k >> 5] >> (k & 31)) & 1u)) continue;
-    uint64_t len = n - st[k] < b ? n - st[k] : b;
-    uint64_t first = (mr[k >> 5] + __popc(mw[k >> 5] & ((1u << (k & 31)) - 1u))) * (uint64_t)arity;
-    uint64_t nch = (len + bn - 1) / bn;
-    uint32_t acc = 0;
-    for (uint64_t i = 0; i < nch; i++) acc += cget(child_cnt, child_cw, (first + i) * S + s);
-    cput(cnt, cw, k * S + s, acc);
+    const uint64_t len = n - st[k] < b ? n - st[k] : b;
+    const uint64_t first = (mr[k >> 5] + __popc(mw[k >> 5] & ((1u << (k & 31)) - 1u))) * (uint64_t)arity;
+    const uint64_t nch = (len + bn - 1) / bn;
+    for (uint32_t s = lane; s < S; s += 32) {
+      uint32_t acc = 0;
+      for (uint64_t i = 0; i < nch; i++) acc += cget(child_cnt, child_cw, (first + i) * S + s);
+      cput(cnt, cw, k * S + s, acc);
+    }
   }
 }
 
@@ -396,7 +399,7 @@ int build_counters(BuildCtx& ctx) {
     }
     if (!last) {
       const Level& w = t->lv[l + 1];
-      BT_LAUNCH(k_sum_children<<<grid_for(v.c * S, T), T, 0, s>>>(v.c, v.b, t->n, v.st, v.mw, v.mr, v.arity, w.b,
+      BT_LAUNCH(k_sum_children<<<grid_for(v.c * 32, T), T, 0, s>>>(v.c, v.b, t->n, v.st, v.mw, v.mr, v.arity, w.b,
                                                         w.cnt, w.cw, S, v.cnt, v.cw));
     }
     BT_CUDA(cudaGetLastError());

@@ -147,8 +147,16 @@ __global__ void __launch_bounds__(kTile) k_kr_local(M m, const uint8_t* __restri
   uint64_t h = 0;
   if (j < nchunks) {
     const uint8_t* p = T + j * kPrefixStride;
+    if ((((uintptr_t)p) & 15) == 0) {  // two 16-byte loads
+      const uint4 v0 = ((const uint4*)p)[0], v1 = ((const uint4*)p)[1];
+      const uint32_t wv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+      for (int i = 0; i < (int)kPrefixStride; i++)
+        h = m.add(m.mul(h, B), (uint64_t)((wv[i >> 2] >> (8 * (i & 3))) & 0xFFu) + 1);
+    } else {
 #pragma unroll 8
-    for (int i = 0; i < (int)kPrefixStride; i++) h = m.add(m.mul(h, B), (uint64_t)p[i] + 1);
+      for (int i = 0; i < (int)kPrefixStride; i++) h = m.add(m.mul(h, B), (uint64_t)p[i] + 1);
+    }
   }
   h = cta_kr_scan(m, h, pw1, sm);
   if (j < nchunks) Hs[j + 1] = h;
