@@ -344,7 +344,8 @@ struct BuildCtx {
   // chunk j of 128 positions lists its grams at gl_chunk[j] .. gl_chunk[j+1].
   const uint32_t* gl_chunk = nullptr;
   const uint32_t* gl_mx = nullptr;
-  const uint8_t* gl_pos = nullptr;
+  const uint32_t* gl_x = nullptr;  // positions (texts are shorter than 2^32)
+  uint32_t gl_total = 0;
   ~BuildCtx() { arena.release(); }
 };
 

@@ -935,9 +935,9 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_scan_anchor(ScanCtx<M> C0, 
 // The selected-gram list.  On the levels whose block length is a multiple of
 // 128 and whose selection is the default (w = 16, density 1/8), the selected
 // grams of a chunk are the same at every level: their positions and mixed
-// hashes are computed once per build, in 128-byte text chunks (positions of
-// chunk j at gl_chunk[j] .. gl_chunk[j+1] of gl_mx / gl_pos), and those levels
-// read the list instead of rolling the hash again.
+// hashes are computed once per build, in 128-byte text chunks (the grams of
+// chunk j at gl_chunk[j] .. gl_chunk[j+1] of gl_mx / gl_x, positions absolute),
+// and those levels read the list instead of rolling the hash again.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kGlSbits = 3;
 constexpr uint64_t kGlMinText = 8ull << 20;  // smaller texts roll the hash at every level
@@ -949,7 +949,7 @@ template <bool WRITE>
 __global__ void __launch_bounds__(256) k_gl_pass(const uint8_t* __restrict__ T, uint64_t n, uint64_t nchunks,
                                                  uint32_t rb, uint32_t rw, uint32_t sel_max,
                                                  uint32_t* __restrict__ cnt, uint32_t* __restrict__ out_mx,
-                                                 uint8_t* __restrict__ out_pos) {
+                                                 uint32_t* __restrict__ out_x) {
   __shared__ uint32_t slots[256 * kSlotWords];
   uint32_t* slotw = slots + threadIdx.x * kSlotWords;
   const bool aligned16 = (((uintptr_t)T) & 15) == 0;
@@ -973,7 +973,7 @@ __global__ void __launch_bounds__(256) k_gl_pass(const uint8_t* __restrict__ T, 
       if (mx <= sel_max) {
         if (WRITE) {
           out_mx[o] = mx;
-          out_pos[o] = 0;
+          out_x[o] = (uint32_t)p0;
         }
         c++;
       }
@@ -991,7 +991,7 @@ __global__ void __launch_bounds__(256) k_gl_pass(const uint8_t* __restrict__ T, 
           if (mx <= sel_max && i < nx) {
             if (WRITE) {
               out_mx[o + c] = mx;
-              out_pos[o + c] = (uint8_t)i;
+              out_x[o + c] = (uint32_t)(p0 + i);
             }
             c++;
           }
@@ -1011,7 +1011,7 @@ __global__ void __launch_bounds__(256) k_scan_list(ScanCtx<M> C0, GramP gp, uint
                                                    const uint32_t* __restrict__ bitmap_g, uint32_t bm_smem_words,
                                                    const uint32_t* __restrict__ gl_chunk,
                                                    const uint32_t* __restrict__ gl_mx,
-                                                   const uint8_t* __restrict__ gl_pos) {
+                                                   const uint32_t* __restrict__ gl_x) {
   if (C0.ld->anchorless == 1u || C0.ld->tail_anchorless == 2u) return;
   extern __shared__ uint32_t bms[];
   __shared__ unsigned int s_qn;
@@ -1061,7 +1061,7 @@ __global__ void __launch_bounds__(256) k_scan_list(ScanCtx<M> C0, GramP gp, uint
           bt[u] = 0;
           mx[u] = 0;
           if (e + u < e1) {
-            pos[u] = gl_pos[e + u];
+            pos[u] = (uint32_t)(gl_x[e + u] - p0);
             mx[u] = gl_mx[e + u];
             const uint32_t bit = gram_bit(gp, mx[u]);
             bt[u] = bit & 31;
@@ -1073,6 +1073,84 @@ __global__ void __launch_bounds__(256) k_scan_list(ScanCtx<M> C0, GramP gp, uint
           if (pos[u] < nx && ((wv[u] >> bt[u]) & 1u)) record_hit(C, &s_qn, p0 + pos[u], k, mx[u]);
       }
     } while (0);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    C.segn[blockIdx.x] = s_qn;
+    atomicAdd(C.qn, (unsigned long long)s_qn);
+    if (s_qn > C.seg) C.ld->qover = 1u;
+  }
+}
+
+// The list scan of a level whose blocks are all present ([k b, (k+1) b),
+// consecutive): the block of a gram and the end of its run follow from its
+// position, so the whole list is read in order, coalesced, 16 entries per
+// thread and step (16-byte loads), their bitmap loads in flight together.
+// bshift: log2 b when b is a power of two, else 0.
+template <class M>
+__global__ void __launch_bounds__(256) k_scan_stream(ScanCtx<M> C0, GramP gp, uint32_t total, uint32_t bshift,
+                                                     const uint32_t* __restrict__ bitmap_g, uint32_t bm_smem_words,
+                                                     const uint32_t* __restrict__ gl_mx,
+                                                     const uint32_t* __restrict__ gl_x) {
+  if (C0.ld->anchorless == 1u || C0.ld->tail_anchorless == 2u) return;
+  extern __shared__ uint32_t bms[];
+  __shared__ unsigned int s_qn;
+  const ScanCtx<M>& C = C0;
+  const Geo& g = C.g;
+  const uint32_t tail_a = C.ld->tail_a;
+  const uint32_t far_end = C.ld->far_end;
+  const uint32_t Wx = gp.W > far_end ? gp.W : far_end;
+  const uint32_t Wt0 = gp.Wr ? gp.Wr : 1;
+  const uint32_t Wt = tail_a != 0xFFFFFFFFu && tail_a + 1 > Wt0 ? tail_a + 1 : Wt0;
+  for (uint32_t i = threadIdx.x; i < bm_smem_words; i += blockDim.x) bms[i] = bitmap_g[i];
+  if (threadIdx.x == 0) s_qn = 0;
+  __syncthreads();
+  const uint32_t* bitmap = bm_smem_words ? bms : bitmap_g;
+  const uint64_t b = g.b, w = gp.w;
+  constexpr uint32_t U = 16;  // entries per thread and step (four 16-byte loads per array)
+  const uint32_t totalU = (total + U - 1) / U;
+  for (uint64_t eu = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; eu < totalU;
+       eu += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t xs[U], mxs[U], wv[U], bt[U];
+    if (U * eu + U <= total) {
+#pragma unroll
+      for (uint32_t q = 0; q < U / 4; q++) {
+        const uint4 X = ((const uint4*)gl_x)[eu * (U / 4) + q], Y = ((const uint4*)gl_mx)[eu * (U / 4) + q];
+        xs[4 * q] = X.x, xs[4 * q + 1] = X.y, xs[4 * q + 2] = X.z, xs[4 * q + 3] = X.w;
+        mxs[4 * q] = Y.x, mxs[4 * q + 1] = Y.y, mxs[4 * q + 2] = Y.z, mxs[4 * q + 3] = Y.w;
+      }
+    } else {
+#pragma unroll
+      for (uint32_t u = 0; u < U; u++) {
+        xs[u] = U * eu + u < total ? gl_x[U * eu + u] : 0xFFFFFFFFu;
+        mxs[u] = U * eu + u < total ? gl_mx[U * eu + u] : 0;
+      }
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < U; u++) {
+      wv[u] = 0;
+      bt[u] = 32;  // 32: no test
+      const uint64_t x = xs[u];
+      if (x >= g.n) continue;
+      const uint64_t k = bshift ? x >> bshift : x / b;
+      // End of block k and up to two following blocks.
+      const uint64_t av = (k + 3) * b < g.n ? (k + 3) * b : g.n;
+      uint64_t xm = av >= b ? av - b + Wx : 0;
+      if (g.r && av >= g.r) {
+        const uint64_t xr = av - g.r + Wt;
+        if (xr > xm) xm = xr;
+      }
+      const uint64_t gram_end = av + 1 >= w ? av + 1 - w : 0;
+      if (xm > gram_end) xm = gram_end;
+      if (x >= xm) continue;
+      const uint32_t bit = gram_bit(gp, mxs[u]);
+      bt[u] = bit & 31;
+      wv[u] = bitmap[bit >> 5];
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < U; u++)
+      if (bt[u] < 32 && ((wv[u] >> bt[u]) & 1u))
+        record_hit(C, &s_qn, xs[u], bshift ? (uint64_t)xs[u] >> bshift : xs[u] / b, mxs[u]);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1907,9 +1985,15 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
     // chunks are the list's chunks; k_scan_anchor then runs only when the
     // level has keys without an anchor.
     const bool use_list = ctx.gl_chunk && gq.w == 16 && gq.sbits == kGlSbits && b % kAnchorQ == 0;
-    if (use_list)
+    // Every block present: blocks k b .. (k+1) b (the level covers the text).
+    const bool all_present = c == (n + b - 1) / b;
+    if (use_list && all_present)
+      BT_LAUNCH(k_scan_stream<M><<<scan_grid, kScanThreads, (size_t)bm_smem * 4, s>>>(
+          C, gq, ctx.gl_total, (b & (b - 1)) == 0 ? (uint32_t)__builtin_ctzll(b) : 0u, bitmap, bm_smem,
+          ctx.gl_mx, ctx.gl_x));
+    else if (use_list)
       BT_LAUNCH(k_scan_list<M><<<scan_grid, kScanThreads, (size_t)bm_smem * 4, s>>>(
-          C, gq, cpa, bitmap, bm_smem, ctx.gl_chunk, ctx.gl_mx, ctx.gl_pos));
+          C, gq, cpa, bitmap, bm_smem, ctx.gl_chunk, ctx.gl_mx, ctx.gl_x));
     BT_LAUNCH(k_scan_anchor<M, false><<<scan_grid, kScanThreads, smem, s>>>(
         C, gq, cpa, atab, (uint32_t)(acap - 1), bitmap, bm_smem, secbits, use_list ? 1 : 0));
     BT_LAUNCH(k_hits<M><<<scan_grid, 512, 0, s>>>(C, atab, (uint32_t)(acap - 1)));
@@ -2033,16 +2117,16 @@ int all_levels(const M& m, BuildCtx& ctx) {
       uint32_t total = 0;
       BT_CUDA(cudaMemcpyAsync(&total, chunk + nchunks, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx.s));
       BT_CUDA(cudaStreamSynchronize(ctx.s));
-      uint32_t* mx;
-      uint8_t* pos;
+      uint32_t *mx, *xs;
       BT_CUDA(cudaMallocAsync((void**)&mx, (uint64_t)(total ? total : 1) * sizeof(uint32_t), ctx.s));
       lm.p.push_back(mx);
-      BT_CUDA(cudaMallocAsync((void**)&pos, total ? total : 1, ctx.s));
-      lm.p.push_back(pos);
-      BT_LAUNCH(k_gl_pass<true><<<grid, 256, 0, ctx.s>>>(ctx.T, n, nchunks, rb, rw, sel_max, chunk, mx, pos));
+      BT_CUDA(cudaMallocAsync((void**)&xs, (uint64_t)(total ? total : 1) * sizeof(uint32_t), ctx.s));
+      lm.p.push_back(xs);
+      BT_LAUNCH(k_gl_pass<true><<<grid, 256, 0, ctx.s>>>(ctx.T, n, nchunks, rb, rw, sel_max, chunk, mx, xs));
       ctx.gl_chunk = chunk;
       ctx.gl_mx = mx;
-      ctx.gl_pos = pos;
+      ctx.gl_x = xs;
+      ctx.gl_total = total;
     }
   }
   for (uint32_t l = 0; l < t->L; l++) {
@@ -2057,7 +2141,8 @@ int all_levels(const M& m, BuildCtx& ctx) {
   }
   ctx.gl_chunk = nullptr;
   ctx.gl_mx = nullptr;
-  ctx.gl_pos = nullptr;
+  ctx.gl_x = nullptr;
+  ctx.gl_total = 0;
   return BT_OK;
 }
 

@@ -250,10 +250,21 @@ __global__ void __launch_bounds__(32 * kExpandWarps) k_kr_expand(M m, const uint
   if (j < nchunks) {
     uint64_t h = Hs[j];
     const uint64_t p0 = j * kPrefixStride;
+    if (p0 + kPrefixStride <= n && (((uintptr_t)(T + p0)) & 15) == 0) {
+      // A full chunk: its 32 bytes are loaded before the multiply chain.
+      const uint4 v0 = ((const uint4*)(T + p0))[0], v1 = ((const uint4*)(T + p0))[1];
+      const uint32_t wv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+      for (uint32_t i = 0; i < kPrefixStride; i++) {
+        tile[warp][lane][i] = h;
+        h = m.add(m.mul(h, B), (uint64_t)((wv[i >> 2] >> (8 * (i & 3))) & 0xFFu) + 1);
+      }
+    } else {
 #pragma unroll 4
-    for (uint32_t i = 0; i < kPrefixStride; i++) {
-      tile[warp][lane][i] = h;
-      if (p0 + i < n) h = m.add(m.mul(h, B), (uint64_t)T[p0 + i] + 1);
+      for (uint32_t i = 0; i < kPrefixStride; i++) {
+        tile[warp][lane][i] = h;
+        if (p0 + i < n) h = m.add(m.mul(h, B), (uint64_t)T[p0 + i] + 1);
+      }
     }
   }
   __syncwarp();
