@@ -69,6 +69,8 @@ def parse_args():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--cpu-sample-mib", type=int, default=8,
                     help="prefix of the workload the CPU oracle builds per step")
+    ap.add_argument("--cpu-mt-sample-mib", type=int, default=1 << 20,
+                    help="prefix of the workload the multithreaded CPU builder builds (default: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-build and serving measurements")
@@ -192,6 +194,20 @@ def cpu_baseline(text: np.ndarray, w: dict, sample_mib: int, steps: int = 1) -> 
     return {"value": n / sec / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {n} bytes ({n >> 20} MiB) of the workload text, prune on, "
                       f"median of {steps} single-threaded builds"}
+
+
+def cpu_mt_baseline(text: np.ndarray, w: dict, sample_mib: int) -> dict:
+    """The straightforward multithreaded CPU builder (OpenMP, every host core)
+    on a prefix of the workload: the multicore CPU baseline."""
+    import cpu_mt
+    n = min(len(text), sample_mib << 20)
+    sample = np.ascontiguousarray(text[:n])
+    t0 = time.perf_counter()
+    cpu_mt.build_tree(sample, w["tau"], w["leaf"], prune=True)
+    sec = time.perf_counter() - t0
+    return {"value": n / sec / 1e6, "unit": UNIT, "cores": cpu_mt.threads(), "kind": "cpu_mt",
+            "sample": f"first {n} bytes ({n >> 20} MiB) of the workload text, prune on, "
+                      f"one OpenMP build on {cpu_mt.threads()} threads"}
 
 
 def measure_batch(ndocs: int = 512, min_len: int = 4 << 10, max_len: int = 1 << 20,
@@ -411,6 +427,7 @@ def run_ours(args):
         line["serve"] = measure_serve()
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(text, w, args.cpu_sample_mib)
+        line["cpu_mt_baseline"] = cpu_mt_baseline(text, w, args.cpu_mt_sample_mib)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
