@@ -24,7 +24,7 @@ def main(path, builds):
     tot = sum(v[1] for v in agg.values())
     print(f"launches {sum(v[0] for v in agg.values())}, kernel time {tot / builds:.2f} ms per build")
     print(f"{'kernel':44s} {'launches':>8s} {'ms/build':>9s} {'share':>7s}")
-    for k, v in sorted(agg.items(), key=lambda x: -x[1][1])[:20]:
+    for k, v in sorted(agg.items(), key=lambda x: -x[1][1])[:60]:
         print(f"{k:44s} {v[0]:8d} {v[1] / builds:9.3f} {100 * v[1] / tot:6.2f}%")
     for k in per:
         if "scan_anchor" in k or "k_candidates" in k:

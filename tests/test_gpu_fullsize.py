@@ -5,8 +5,9 @@ sampled outputs against the definition (bytes.find gives the leftmost
 occurrence of a sampled block or pair string), properties that hold at any
 size (every pointer copies its source, lies strictly left, targets marked
 blocks; the leaf text is the marked last-level blocks), naive query counts
-for sampled symbols, and equality of the two independent window-scan
-strategies (anchored and dense).
+for sampled symbols, equality of the two independent window-scan strategies
+(anchored and dense), and of the parallel pruning rounds with the sequential
+right-to-left finish.
 """
 import numpy as np
 import pytest
@@ -34,6 +35,11 @@ def test_full_size_workload(name):
     t, blob = _build(d, sigma, tau, leaf)
     _, blob_dense = _build(d, sigma, tau, leaf, dense_scan=True)
     assert blob == blob_dense
+    if name == "text_versions_256MiB":
+        # Pruning by parallel frontier rounds (wide ones on many CTAs, narrow
+        # ones on one) against the sequential right-to-left rule alone.
+        _, blob_seq = _build(d, sigma, tau, leaf, max_rounds=1)
+        assert blob == blob_seq
     p, blocks = check_pointers(T, blob, sample=300)
     check_leftmost_sampled(T, p, blocks, per_level=per_level)
     syms = np.unique(T)[:3]

@@ -271,3 +271,25 @@ def test_anchored_and_dense_scans(scan):
         ref = oracle.build(text, tau, leaf).export()
         _, blob = gpu_export(text, 256, tau, leaf, **kw)
         assert blob == ref, (text, tau, leaf)
+
+
+@pytest.mark.parametrize("max_rounds", [1, 2, 3, 7, 0])
+def test_prune_round_bound(max_rounds):
+    """Pruning decides the same blocks whatever the bound on the parallel
+    frontier rounds (section 3.1's right-to-left rule): the rounds that do not
+    finish leave the rest to the sequential finish; levels of more than 16 Ki
+    blocks start with multi-CTA rounds and hand narrow frontiers to one CTA."""
+    text = workloads.text_versions(n=4 << 20, base_len=64 << 10, sigma=26, seed=21)
+    ref = _prune_ref(text)
+    _, blob = gpu_export(text, 26, 4, 8, prune=True, max_rounds=max_rounds)
+    assert blob == ref
+
+
+_PRUNE_REF = {}
+
+
+def _prune_ref(text):
+    key = hash(text.tobytes())
+    if key not in _PRUNE_REF:
+        _PRUNE_REF[key] = oracle.build(text, 4, 8, prune=True).export()
+    return _PRUNE_REF[key]
