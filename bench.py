@@ -202,9 +202,12 @@ def cpu_mt_baseline(text: np.ndarray, w: dict, sample_mib: int) -> dict:
     import cpu_mt
     n = min(len(text), sample_mib << 20)
     sample = np.ascontiguousarray(text[:n])
-    t0 = time.perf_counter()
-    cpu_mt.build_tree(sample, w["tau"], w["leaf"], prune=True)
-    sec = time.perf_counter() - t0
+    try:
+        t0 = time.perf_counter()
+        cpu_mt.build_tree(sample, w["tau"], w["leaf"], prune=True)
+        sec = time.perf_counter() - t0
+    except (OSError, RuntimeError, subprocess.CalledProcessError) as e:
+        return {"unavailable": f"multithreaded CPU builder failed: {e}"}
     return {"value": n / sec / 1e6, "unit": UNIT, "cores": cpu_mt.threads(), "kind": "cpu_mt",
             "sample": f"first {n} bytes ({n >> 20} MiB) of the workload text, prune on, "
                       f"one OpenMP build on {cpu_mt.threads()} threads"}
