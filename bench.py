@@ -74,7 +74,41 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-build and serving measurements")
+    ap.add_argument("--summarize-launches", metavar="CSV",
+                    help="summarize an ncu launch list (--metrics gpu__time_duration.sum --csv) and exit")
+    ap.add_argument("--builds", type=int, default=1,
+                    help="builds the launch list covers (with --summarize-launches)")
     return ap.parse_args()
+
+
+def summarize_launches(path: str, builds: int) -> None:
+    """Per kernel of an ncu launch list: launches, time per build and share of
+    the kernel time; then the per-level durations of the window-scan kernels
+    of one build (the launch list's second build, after the warm-up)."""
+    import collections
+    import csv
+    rows = [r for r in csv.reader(open(path)) if len(r) > 10]
+    hdr, rows = rows[0], rows[1:]
+    i_name, i_val = hdr.index("Kernel Name"), hdr.index("Metric Value")
+    agg = collections.defaultdict(lambda: [0, 0.0])
+    per = collections.defaultdict(list)
+    for r in rows:
+        name = r[i_name].split("(")[0].replace("void ", "").replace("(anonymous namespace)::", "")
+        name = name.replace("unnamed>::", "")
+        ms = float(r[i_val].replace(",", "")) / 1e6
+        agg[name][0] += 1
+        agg[name][1] += ms
+        per[name].append(ms)
+    tot = sum(v[1] for v in agg.values())
+    print(f"launches {sum(v[0] for v in agg.values())}, kernel time {tot / builds:.2f} ms per build")
+    print(f"{'kernel':44s} {'launches':>8s} {'ms/build':>9s} {'share':>7s}")
+    for k, v in sorted(agg.items(), key=lambda x: -x[1][1])[:40]:
+        print(f"{k:44s} {v[0]:8d} {v[1] / builds:9.3f} {100 * v[1] / tot:6.2f}%")
+    for k in per:
+        if any(s in k for s in ("k_scan_stream", "k_scan_list", "k_scan_anchor", "k_hits", "k_candidates<")):
+            n = len(per[k]) // builds
+            lo = n if builds > 1 else 0
+            print(k, "per level:", " ".join(f"{x:.3f}" for x in per[k][lo:lo + n]))
 
 
 def measured_peaks() -> dict:
@@ -384,8 +418,8 @@ def run_ours(args):
     ratio = recorded_traffic("window_scan")
     per_launch_bytes = scan["bytes"] / max(1, scan["launches"])
     roofline = {
-        "kernel": "window scan of a level (k_anchor_keys, k_scan_list/k_scan_anchor, k_hits, "
-                  "k_candidates)",
+        "kernel": "window scan of a level (k_scan_stream or k_scan_list, k_scan_anchor, k_hits, "
+                  "k_candidates, and the tail-key k_scan)",
         "bound": "hbm",
         "achieved": achieved,
         "peak": hbm if hbm else 6800.0,
@@ -438,7 +472,9 @@ def run_ours(args):
 
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.summarize_launches:
+        summarize_launches(args.summarize_launches, args.builds)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
