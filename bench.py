@@ -54,7 +54,8 @@ WORKLOADS = {
     "dna_genome_2GiB": dict(
         gen=lambda: workloads.dna_genome(), sigma=5, tau=4, leaf=64,
         desc="2 GiB DNA: 32 MiB uniform ACGT genome, 64 copies with 0.1% SNPs, "
-             "0.01% indels of 1-50 bases, N runs"),
+             "0.01% indels of 1-50 bases, N runs",
+        opts={"two_phase": True}),
 }
 DEFAULT_WORKLOAD = "text_versions_256MiB"
 SCAN_SOURCE = os.path.join(ROOT, "paper_2512_23314_gb300", "csrc", "bt_level.cu")
@@ -348,7 +349,7 @@ def run_ours(args):
     n = len(text)
     d_text = torch.from_numpy(text).cuda()
     stream = torch.cuda.current_stream()
-    opts = bt.BuildOptions(prune=True).to_c()[0]
+    opts = bt.BuildOptions(prune=True, **w.get("opts", {})).to_c()[0]
 
     def step(src):
         h = bt.bt_build_ex(src, n, w["sigma"], w["tau"], w["leaf"], opts, stream)
@@ -446,7 +447,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": args.workload, "n": n, "sigma": w["sigma"], "tau": w["tau"],
-                   "leaf_len": w["leaf"], "prune": True, "levels": len(stats),
+                   "leaf_len": w["leaf"], "prune": True, "build_options": w.get("opts", {}),
+                   "levels": len(stats),
                    "sum_cov_bytes": cov, "verify_bytes": vbytes, "scan_candidates": cands,
                    "scan_hits": hits,
                    "l2": "input (n bytes) larger than the 129 MB L2; no flush",

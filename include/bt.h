@@ -79,7 +79,16 @@ typedef struct {
 /* BT_FLAG_GRAM_LIST builds the selected-gram list (the gram positions and
  * hashes the anchored scan shares between levels) whatever the text length;
  * by default only texts of 8 MiB or more use it (a test hook; same tree). */
-enum { BT_FLAG_DENSE_SCAN = 1, BT_FLAG_TINY_QUEUE = 2, BT_FLAG_GRAM_LIST = 4 };
+/* BT_FLAG_TWO_PHASE tests the proposed windows of every anchored level in two
+ * phases: the windows of the gram hits in the first 1/16 of the text, then
+ * the rest, against per-gram bounds lowered to the leftmost positions found so
+ * far (a window after every such position of the keys on its gram is not
+ * proposed).  The same tree.  It pays where the keys on a gram mostly have
+ * their leftmost occurrence early (DNA copies with sparse point mutations:
+ * about a third fewer windows); where most grams also carry a key first seen
+ * late (edits in every copy of a versioned text) few windows are saved and the
+ * two extra kernels and the second hit pass cost more, hence off by default. */
+enum { BT_FLAG_DENSE_SCAN = 1, BT_FLAG_TINY_QUEUE = 2, BT_FLAG_GRAM_LIST = 4, BT_FLAG_TWO_PHASE = 8 };
 
 void bt_opts_default(bt_opts* opts);
 

@@ -22,6 +22,7 @@ BT_Q_ACCESS, BT_Q_RANK, BT_Q_SELECT = 0, 1, 2
 BT_FLAG_DENSE_SCAN = 1
 BT_FLAG_TINY_QUEUE = 2
 BT_FLAG_GRAM_LIST = 4
+BT_FLAG_TWO_PHASE = 8
 ST_FIELDS = 10
 ST_NAMES = ("nblocks", "b", "cov", "nmarked", "npairs", "verify_bytes", "collisions",
             "final_blocks", "candidates", "hits")
@@ -283,6 +284,7 @@ class BuildOptions:
     dense_scan: bool = False
     tiny_queue: bool = False  # test hook: forces the scan's queue-overflow path
     gram_list: bool = False  # test hook: selected-gram list whatever the text length
+    two_phase: bool = False  # two-phase window tests on every anchored level (same tree)
 
     def to_c(self):
         o = bt_opts_default()
@@ -293,7 +295,8 @@ class BuildOptions:
         o.max_rounds = self.max_rounds
         o.flags = ((BT_FLAG_DENSE_SCAN if self.dense_scan else 0)
                    | (BT_FLAG_TINY_QUEUE if self.tiny_queue else 0)
-                   | (BT_FLAG_GRAM_LIST if self.gram_list else 0))
+                   | (BT_FLAG_GRAM_LIST if self.gram_list else 0)
+                   | (BT_FLAG_TWO_PHASE if self.two_phase else 0))
         keep = None
         if self.level_sizes is not None:
             keep = np.ascontiguousarray(self.level_sizes, dtype=np.uint64)

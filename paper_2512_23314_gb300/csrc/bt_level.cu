@@ -361,9 +361,10 @@ __device__ __forceinline__ uint32_t sec_bit(uint32_t mx) { return (mx * 0x2545F4
 // Register the anchor of every key (every block and the tail).
 __global__ void k_anchor_keys(Geo g, GramP gp, const uint32_t* __restrict__ slotB, AnchorSet* atab,
                               uint32_t amask, FarNode* fnode, uint32_t fcap, uint32_t* bitmap,
-                              uint32_t* secbits, LevelDev* ld, Status* status) {
+                              uint32_t* secbits, uint32_t* __restrict__ aidx, LevelDev* ld, Status* status) {
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < g.c;
        k += (uint64_t)gridDim.x * blockDim.x) {
+    aidx[k] = kNoSlot;
     const uint64_t s = g.st[k], len = blen(g, k);
     const bool tail = len != g.b;
     uint32_t Wk;
@@ -395,12 +396,13 @@ __global__ void k_anchor_keys(Geo g, GramP gp, const uint32_t* __restrict__ slot
     const uint32_t gk = gram_key(mx);
     bool sec = a == kNoSlot;
     if (!sec && !tail) {
-      uint32_t h = gram_slot(gk, amask);
+      uint32_t h = gram_slot(gk, amask), hp = kNoSlot;
       bool placed = false;
       for (uint32_t it = 0; it <= amask && !placed; it++) {
         const uint32_t cur = atomicCAS(&atab[h].gram, kEmptyGram, gk);
         if (cur == kEmptyGram || cur == gk) {
           placed = true;
+          hp = h;
           if (a < Wk) {
             atomicOr(&atab[h].offs, 1ull << a);
           } else {
@@ -422,6 +424,7 @@ __global__ void k_anchor_keys(Geo g, GramP gp, const uint32_t* __restrict__ slot
         }
       }
       if (!placed) atomicExch(&status->error, 7ull);
+      if (placed && !sec) aidx[k] = hp;
     }
     if (sec) {  // no usable anchor: registered by its first gram
       const uint32_t sb = sec_bit(mx0);
@@ -1162,9 +1165,13 @@ __global__ void __launch_bounds__(256) k_scan_stream(ScanCtx<M> C0, GramP gp, ui
 
 // The hits of scan CTA j's segment, one per thread: anchor-table lookup; the
 // windows the anchors propose go to this CTA's candidate segment.
+// With BT_FLAG_TWO_PHASE the windows of a level are tested in two phases:
+// first those of the hits in the first 1/16 of the text, then the rest.
+__device__ __forceinline__ uint64_t hit_split(const Geo& g) { return g.n >> 4; }
+
 template <class M>
 __global__ void __launch_bounds__(512) k_hits(ScanCtx<M> C0, const AnchorSet* __restrict__ atab,
-                                              uint32_t amask) {
+                                              uint32_t amask, uint32_t phase) {
   __shared__ unsigned int s_cn;
   if (threadIdx.x == 0) s_cn = 0;
   __syncthreads();
@@ -1177,6 +1184,10 @@ __global__ void __launch_bounds__(512) k_hits(ScanCtx<M> C0, const AnchorSet* __
   const uint32_t sn = C.segn[blockIdx.x];
   const uint32_t n = sn < C.seg ? sn : C.seg;
   const Hit* q = C.q + blockIdx.x * (uint64_t)C.seg;
+  // phase 0: every hit; 1: hits before the split; 2: hits from the split on.
+  uint64_t x_lo = 0, x_hi = ~0ull;
+  if (phase == 1) x_hi = hit_split(g);
+  if (phase == 2) x_lo = hit_split(g);
   uint32_t ncand = 0, nhit = 0;
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
     const Hit e = q[i];
@@ -1185,6 +1196,7 @@ __global__ void __launch_bounds__(512) k_hits(ScanCtx<M> C0, const AnchorSet* __
       atomicExch(&C.status->error, 9ull);
       continue;
     }
+    if (x < x_lo || x >= x_hi) continue;
     const uint64_t k = e.k, s = g.st[k], av = avail_end(g, k);
     if (e.x & kHitSec) {
       if (anchorless) propose(C, &s_cn, k, s, av, x, 0, ncand, nhit);
@@ -1197,6 +1209,37 @@ __global__ void __launch_bounds__(512) k_hits(ScanCtx<M> C0, const AnchorSet* __
   if (threadIdx.x == 0) {
     C.csegn[blockIdx.x] = s_cn;
     if (s_cn > C.cseg) C.ld->qover = 1u;
+  }
+}
+
+// Between the two phases of a level: each gram's bound on useful window
+// starts (AnchorSet::maxst, first the largest start of a key anchored on it)
+// drops to the largest current leftmost position among its keys, counting the
+// pairs that start with them and the pair ending in the tail.  A window that
+// starts after all of these cannot lower any of them, so the second phase
+// proposes fewer windows and finds the same minima.  step 0 clears the bound
+// of every gram that holds an anchored key, step 1 raises it again.
+__global__ void k_anchor_bound(Geo g, const uint32_t* __restrict__ aidx, const uint32_t* __restrict__ slotB,
+                               const uint32_t* __restrict__ slotP, const BSlot* __restrict__ bt,
+                               const PSlot* __restrict__ pt, AnchorSet* atab, const LevelDev* ld, int step) {
+  const uint32_t pretail = ld->pretail_slot;
+  const unsigned long long ltp = ld->lo_tailpair;
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < g.c;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t h = aidx[k];
+    if (h == kNoSlot) continue;
+    if (step == 0) {
+      atab[h].maxst = 0;
+      continue;
+    }
+    const uint32_t sb = slotB[k];
+    unsigned long long hi = bt[sb].lo;
+    if (k + 1 < g.c) {
+      const uint32_t sp = slotP[k];
+      if (sp != kNoSlot && sp != kTailPair && pt[sp].lo > hi) hi = pt[sp].lo;
+    }
+    if (g.r && sb == pretail && ltp > hi) hi = ltp;
+    atomicMax(&atab[h].maxst, hi);
   }
 }
 
@@ -1906,6 +1949,7 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
   Cand* cq = nullptr;
   uint32_t* csegn = nullptr;
   unsigned long long* qn = nullptr;
+  uint32_t* aidx = nullptr;
   auto carve = [&]() {
     W.fpB = A.take<uint64_t>(c);
     W.slotB = A.take<uint32_t>(c);
@@ -1932,6 +1976,7 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
       cq = A.take<Cand>((uint64_t)seg * scan_grid);
       csegn = A.take<uint32_t>(scan_grid);
       qn = A.take<unsigned long long>(1);
+      aidx = A.take<uint32_t>(c);
     }
   };
   A.begin_dry();
@@ -1970,7 +2015,7 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
                                                             W.ld, 0));
   } else {
     BT_LAUNCH(k_anchor_keys<<<gc, T, 0, s>>>(g, gq, W.slotB, atab, (uint32_t)(acap - 1), fnode, fcap, bitmap, secbits,
-                                             W.ld, ctx.st));
+                                             aidx, W.ld, ctx.st));
     ScanCtx<M> C{m, g, W.bt, bcap - 1, W.pt, pcap - 1, W.ld, 0, 0,
                  q, segn, seg, qn, cq, csegn, seg, ctx.st, fnode, W.slotB};
     const size_t smem_base = ((size_t)kSecBits / 32 + (size_t)kRing * kScanThreads +
@@ -1996,7 +2041,17 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
           C, gq, cpa, bitmap, bm_smem, ctx.gl_chunk, ctx.gl_mx, ctx.gl_x));
     BT_LAUNCH(k_scan_anchor<M, false><<<scan_grid, kScanThreads, smem, s>>>(
         C, gq, cpa, atab, (uint32_t)(acap - 1), bitmap, bm_smem, secbits, use_list ? 1 : 0));
-    BT_LAUNCH(k_hits<M><<<scan_grid, 512, 0, s>>>(C, atab, (uint32_t)(acap - 1)));
+    if (ctx.two_phase) {
+      // Two phases: the hits in the first 1/16 of the text, then the rest
+      // against the bounds the first phase tightened.
+      BT_LAUNCH(k_hits<M><<<scan_grid, 512, 0, s>>>(C, atab, (uint32_t)(acap - 1), 1u));
+      BT_LAUNCH(k_candidates<M><<<scan_grid, 256, 0, s>>>(C));
+      for (int step = 0; step < 2; step++)
+        BT_LAUNCH(k_anchor_bound<<<gc, T, 0, s>>>(g, aidx, W.slotB, W.slotP, W.bt, W.pt, atab, W.ld, step));
+      BT_LAUNCH(k_hits<M><<<scan_grid, 512, 0, s>>>(C, atab, (uint32_t)(acap - 1), 2u));
+    } else {
+      BT_LAUNCH(k_hits<M><<<scan_grid, 512, 0, s>>>(C, atab, (uint32_t)(acap - 1), 0u));
+    }
     BT_LAUNCH(k_candidates<M><<<scan_grid, 256, 0, s>>>(C));
     // Only when the queue overflowed: the scan again, testing windows inline.
     BT_LAUNCH(k_scan_anchor<M, true><<<scan_grid, kScanThreads, smem, s>>>(

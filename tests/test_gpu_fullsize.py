@@ -6,8 +6,8 @@ occurrence of a sampled block or pair string), properties that hold at any
 size (every pointer copies its source, lies strictly left, targets marked
 blocks; the leaf text is the marked last-level blocks), naive query counts
 for sampled symbols, equality of the two independent window-scan strategies
-(anchored and dense), and of the parallel pruning rounds with the sequential
-right-to-left finish.
+(anchored and dense), of the one- and two-phase window tests, and of the
+parallel pruning rounds with the sequential right-to-left finish.
 """
 import numpy as np
 import pytest
@@ -40,6 +40,10 @@ def test_full_size_workload(name):
         # ones on one) against the sequential right-to-left rule alone.
         _, blob_seq = _build(d, sigma, tau, leaf, max_rounds=1)
         assert blob == blob_seq
+    else:
+        # The two-phase window tests the bench uses on this workload.
+        _, blob_two = _build(d, sigma, tau, leaf, two_phase=True)
+        assert blob == blob_two
     p, blocks = check_pointers(T, blob, sample=300)
     check_leftmost_sampled(T, p, blocks, per_level=per_level)
     syms = np.unique(T)[:3]

@@ -241,14 +241,15 @@ def _far_anchor_text(n, seed):
     return np.frombuffer(bytes(out[:n]), np.uint8)
 
 
-@pytest.mark.parametrize("scan", ["anchored", "dense", "tiny_queue", "gram_list"])
+@pytest.mark.parametrize("scan", ["anchored", "dense", "tiny_queue", "gram_list", "two_phase"])
 def test_anchored_and_dense_scans(scan):
     """Both window-scan strategies give the oracle's tree, including texts whose
     keys have no anchor (long runs) and short tails of every length; so does
     the anchored scan whose candidate queue overflows at every level, and the
-    one that reads the selected-gram list."""
+    one that reads the selected-gram list, and the one that tests the windows of
+    every level in two phases (the second against bounds the first tightened)."""
     kw = {"dense_scan": scan == "dense", "tiny_queue": scan == "tiny_queue",
-          "gram_list": scan == "gram_list"}
+          "gram_list": scan == "gram_list", "two_phase": scan == "two_phase"}
     cases = [
         (_runs_text(50_000, 1), 2, 8), (_runs_text(120_001, 2, b"abc", 500), 4, 16),
         (_runs_text(30_000, 3, b"a", 2), 2, 4), (np.full(100_003, 65, np.uint8), 4, 32),
