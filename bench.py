@@ -58,6 +58,7 @@ WORKLOADS = {
         opts={"two_phase": True}),
 }
 DEFAULT_WORKLOAD = "text_versions_256MiB"
+HBM_SPEC_GBS = 8000.0  # nominal HBM3e bandwidth of a GB300
 SCAN_SOURCE = os.path.join(ROOT, "paper_2512_23314_gb300", "csrc", "bt_level.cu")
 
 
@@ -229,6 +230,27 @@ def cpu_baseline(text: np.ndarray, w: dict, sample_mib: int, steps: int = 1) -> 
     return {"value": n / sec / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {n} bytes ({n >> 20} MiB) of the workload text, prune on, "
                       f"median of {steps} single-threaded builds"}
+
+
+def int_roofline(bt, torch, stream, mulmods_per_step: int, step_ms: float) -> dict:
+    """The integer-pipe roofline of the build: the measured rate of the 61-bit
+    modular multiply (the library's microbenchmark, one CTA of 256 threads
+    per SM slot, 8 independent chains per thread) against the algorithmic
+    multiplies of a step (one per window and length: 2 x the covered bytes)."""
+    blocks = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count * 8
+    out = torch.empty(blocks * 256, dtype=torch.int64, device="cuda")
+    bt.bt_mulmod_bench(blocks, 64, out, stream)  # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    n = bt.bt_mulmod_bench(blocks, 4096, out, stream)
+    e1.record(stream)
+    e1.synchronize()
+    rate = n / (e0.elapsed_time(e1) / 1e3)
+    t_roof_ms = mulmods_per_step / rate * 1e3
+    return {"bound": "alu", "work": "one 61-bit modular multiply per window and length (2 x covered bytes)",
+            "mulmods_per_step": mulmods_per_step, "peak": rate / 1e12, "unit": "Tmulmod/s",
+            "peak_source": f"measured: {n} multiplies in {e0.elapsed_time(e1):.3f} ms",
+            "t_roof_ms": t_roof_ms, "frac": t_roof_ms / step_ms if step_ms > 0 else None}
 
 
 def cpu_mt_baseline(text: np.ndarray, w: dict, sample_mib: int) -> dict:
@@ -427,21 +449,27 @@ def run_ours(args):
         "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "of fallback",
         "unit": "GB/s",
         "frac": (achieved / hbm) if (achieved and hbm) else None,
+        "frac_of_spec": (achieved / HBM_SPEC_GBS) if achieved else None,
         "traffic": (ratio * per_launch_bytes) if ratio is not None else None,
         "alg_bytes_per_launch": per_launch_bytes,
         "launches": scan["launches"],
         "share_of_step": (scan["ms"] / ms) if ms > 0 else None,
     }
     cov = sum(s["cov"] for s in stats)
+    int_roof = int_roofline(bt, torch, stream, 2 * cov, ms / args.steps)
     vbytes = sum(s["verify_bytes"] for s in stats)
     cands = sum(s["candidates"] for s in stats)
     hits = sum(s["hits"] for s in stats)
     # The whole build against the same peak (B_alg = n + sum cov + V + S, S the tree's bytes).
     alg_build = n + cov + vbytes + tree_bytes
     build_gbs = alg_build / (ms / args.steps / 1e3) / 1e9 * world if ms > 0 else None
+    t_hbm_ms = alg_build / ((hbm if hbm else 6800.0) * 1e9) * 1e3
     build_roofline = {"alg_bytes_per_step": alg_build, "achieved": build_gbs,
                       "peak": hbm if hbm else 6800.0, "unit": "GB/s",
-                      "frac": (build_gbs / hbm) if (build_gbs and hbm) else None}
+                      "frac": (build_gbs / hbm) if (build_gbs and hbm) else None,
+                      "frac_of_spec": (build_gbs / HBM_SPEC_GBS) if build_gbs else None,
+                      "t_roof_hbm_ms": t_hbm_ms, "t_roof_int_ms": int_roof["t_roof_ms"],
+                      "binding": "int" if int_roof["t_roof_ms"] > t_hbm_ms else "hbm"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -455,6 +483,7 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roofline,
         "build_roofline": build_roofline,
+        "int_roofline": int_roof,
         "kernels_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n,
                 "d2h_bytes_per_step": d2h},

@@ -241,6 +241,18 @@ int bt_profile_read(bt_profile_entry* out, uint32_t cap, uint32_t* count);
 /* Number of kernels this library has launched in the process so far. */
 uint64_t bt_launch_count(void);
 
+/* Integer-pipe microbenchmark for the roofline of the fingerprint arithmetic
+ * (section 2: one 61-bit modular multiply per window and length).  Launches,
+ * on `stream` (NULL: the per-thread default stream), `blocks` CTAs of 256
+ * threads that each run 8 independent chains of `iters` multiplies mod
+ * 2^61-1 by the base of `seed`, and store one word per thread in d_out
+ * (device memory, blocks * 256 u64, owned by the caller).  *mulmods receives
+ * the number of multiplies launched; the caller times the launch (CUDA events
+ * on the same stream).  BT_EINVAL for null pointers or zero sizes, BT_ECUDA
+ * when the launch fails.  Returns without waiting. */
+int bt_mulmod_bench(uint32_t blocks, uint32_t iters, uint64_t seed, uint64_t* d_out, void* stream,
+                    uint64_t* mulmods);
+
 #ifdef __cplusplus
 }
 #endif

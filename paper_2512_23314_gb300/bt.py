@@ -85,9 +85,10 @@ def lib() -> ctypes.CDLL:
     L.bt_profile_read.argtypes = [vp, u32, P(u32)]
     L.bt_launch_count.argtypes = []
     L.bt_launch_count.restype = u64
+    L.bt_mulmod_bench.argtypes = [u32, u32, u64, vp, vp, P(u64)]
     for name in ("bt_profile_read", "bt_build", "bt_build_ex", "bt_build_batch", "bt_access", "bt_rank", "bt_select",
                  "bt_query_batch", "bt_export", "bt_stats", "bt_prefix_fingerprints",
-                 "bt_prefix_fingerprints_noalloc"):
+                 "bt_prefix_fingerprints_noalloc", "bt_mulmod_bench"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -271,6 +272,16 @@ def bt_profile_read() -> dict:
 
 def bt_launch_count() -> int:
     return int(lib().bt_launch_count())
+
+
+def bt_mulmod_bench(blocks: int, iters: int, d_out, stream=None, seed: int = 0) -> int:
+    """Launch the modular-multiply microbenchmark on `stream` (a torch stream
+    or None); d_out is a device tensor of blocks * 256 int64.  Returns the
+    number of multiplies launched (time the launch with CUDA events)."""
+    n = ctypes.c_uint64()
+    _check(lib().bt_mulmod_bench(blocks, iters, seed, ctypes.c_void_p(d_out.data_ptr()), _stream_ptr(stream),
+                                 ctypes.byref(n)), "bt_mulmod_bench")
+    return int(n.value)
 
 
 @dataclass

@@ -416,5 +416,40 @@ extern "C" int bt_prefix_fingerprints_noalloc(const uint8_t* d_text, uint64_t n,
 }
 
 namespace bt {
+namespace {
 
+// Integer-pipe microbenchmark: kMulChains independent chains of the 61-bit
+// modular multiply the fingerprints use, `iters` steps each, per thread.  The
+// base arrives at run time and every chain's result is stored, so nothing
+// folds away.
+constexpr int kMulChains = 8;
+
+__global__ void __launch_bounds__(256) k_mulmod_bench(uint64_t B, uint32_t iters, uint64_t* __restrict__ out) {
+  const Mersenne61 m;
+  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  uint64_t a[kMulChains];
+#pragma unroll
+  for (int u = 0; u < kMulChains; u++) a[u] = (t * kMulChains + u) % (Mersenne61::Q - 1) + 1;
+  for (uint32_t i = 0; i < iters; i++) {
+#pragma unroll
+    for (int u = 0; u < kMulChains; u++) a[u] = m.mul(a[u], B);
+  }
+  uint64_t x = 0;
+#pragma unroll
+  for (int u = 0; u < kMulChains; u++) x ^= a[u];
+  out[t] = x;
+}
+
+}  // namespace
 }  // namespace bt
+
+extern "C" int bt_mulmod_bench(uint32_t blocks, uint32_t iters, uint64_t seed, uint64_t* d_out, void* stream,
+                               uint64_t* mulmods) {
+  using namespace bt;
+  if (!d_out || !mulmods || blocks == 0 || iters == 0) return BT_EINVAL;
+  cudaStream_t s = stream ? (cudaStream_t)stream : cudaStreamPerThread;
+  BT_LAUNCH(k_mulmod_bench<<<blocks, 256, 0, s>>>(bt_fingerprint_base(seed, 0), iters, d_out));
+  BT_CUDA(cudaGetLastError());
+  *mulmods = (uint64_t)blocks * 256 * iters * kMulChains;
+  return BT_OK;
+}

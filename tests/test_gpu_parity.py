@@ -294,3 +294,21 @@ def _prune_ref(text):
     if key not in _PRUNE_REF:
         _PRUNE_REF[key] = oracle.build(text, 4, 8, prune=True).export()
     return _PRUNE_REF[key]
+
+
+def test_mulmod_bench_values():
+    """The integer-pipe microbenchmark runs the fingerprint multiply: every
+    chain ends at a0 * B^iters mod 2^61 - 1 (B the base of the seed)."""
+    blocks, iters, seed = 2, 100, 5
+    out = torch.empty(blocks * 256, dtype=torch.int64, device="cuda")
+    n = bt.bt_mulmod_bench(blocks, iters, out, None, seed=seed)
+    torch.cuda.synchronize()
+    assert n == blocks * 256 * iters * 8
+    q = (1 << 61) - 1
+    bi = pow(oracle.base(seed), iters, q)
+    vals = out.cpu().numpy().view(np.uint64)
+    for t in (0, 1, 255, 256, 511):
+        x = 0
+        for u in range(8):
+            x ^= ((t * 8 + u) % (q - 1) + 1) * bi % q
+        assert int(vals[t]) == x
