@@ -76,6 +76,12 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-build and serving measurements")
+    ap.add_argument("--batch-docs", type=int, default=512,
+                    help="documents of the batched-build measurement (8192: the full batched workload)")
+    ap.add_argument("--batch-max-mib", type=int, default=1,
+                    help="largest document of the batched-build measurement in MiB (16: the full workload)")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the batched-build measurement and print its JSON object")
     ap.add_argument("--summarize-launches", metavar="CSV",
                     help="summarize an ncu launch list (--metrics gpu__time_duration.sum --csv) and exit")
     ap.add_argument("--builds", type=int, default=1,
@@ -278,7 +284,9 @@ def measure_batch(ndocs: int = 512, min_len: int = 4 << 10, max_len: int = 1 << 
     import torch
 
     from paper_2512_23314_gb300 import bt
+    t_gen = time.perf_counter()
     docs = workloads.doc_mix(ndocs, min_len=min_len, max_len=max_len, seed=0xB7EE0004)
+    gen_s = time.perf_counter() - t_gen
     args = ([d.text for d in docs], [len(d.text) for d in docs], [d.sigma for d in docs],
             [d.tau for d in docs], [d.leaf_len for d in docs])
     warm = bt.bt_build_batch(*(a[:16] for a in args), nworkers=nworkers)
@@ -301,6 +309,7 @@ def measure_batch(ndocs: int = 512, min_len: int = 4 << 10, max_len: int = 1 << 
     total = sum(len(d.text) for d in docs)
     return {"workload": f"{ndocs} versioned-text documents, log-uniform {min_len >> 10} KiB - "
                         f"{max_len >> 20} MiB, sigma 4-128, tau 2/4/8, leaf 32",
+            "generate_s": gen_s,
             "docs": ndocs, "bytes": total, "nworkers": nworkers,
             "docs_per_s": ndocs / batch_s, "plain_docs_per_s": ndocs / plain_s,
             "speedup": plain_s / batch_s, "batch_mb_per_s": total / batch_s / 1e6,
@@ -491,7 +500,7 @@ def run_ours(args):
         "clocks": clocks,
     }
     if world == 1 and not args.no_extras:
-        line["batch"] = measure_batch()
+        line["batch"] = measure_batch(args.batch_docs, max_len=args.batch_max_mib << 20)
         line["serve"] = measure_serve()
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(text, w, args.cpu_sample_mib)
@@ -505,6 +514,10 @@ def main():
     args = parse_args()
     if args.summarize_launches:
         summarize_launches(args.summarize_launches, args.builds)
+    elif args.batch_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(measure_batch(args.batch_docs, max_len=args.batch_max_mib << 20)), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:
