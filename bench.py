@@ -318,7 +318,9 @@ def measure_batch(ndocs: int = 512, min_len: int = 4 << 10, max_len: int = 1 << 
 
 def measure_serve(rate: float = 2000.0, duration: float = 0.25, min_len: int = 1 << 10,
                   max_len: int = 2 << 20, nworkers: int = 16) -> dict:
-    """The serving loop on a scaled-down arrival stream."""
+    """The serving loop on a scaled-down arrival stream: 0.25 s of Poisson
+    arrivals of documents of 1 KiB - 2 MiB (the full stream offers ~120 GB of
+    text, too much to generate within a bench run)."""
     from paper_2512_23314_gb300 import serve
     arrivals = workloads.serve_arrivals(rate=rate, duration=duration, min_len=min_len,
                                         max_len=max_len)

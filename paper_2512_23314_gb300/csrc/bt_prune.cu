@@ -124,7 +124,7 @@ __global__ void k_indegree(PView v, const uint32_t* __restrict__ state, const ui
   }
 }
 
-// Round 0: candidates nothing targets are pruned; they form the first
+// Frontier round 0: candidates nothing targets are pruned; they form the first
 // worklist (fq[0, prog[0])).
 __global__ void k_round0(PView v, uint32_t* __restrict__ state, const uint32_t* __restrict__ indeg,
                          uint32_t* __restrict__ fq, unsigned long long* prog) {
