@@ -238,6 +238,43 @@ def cpu_baseline(text: np.ndarray, w: dict, sample_mib: int, steps: int = 1) -> 
                       f"median of {steps} single-threaded builds"}
 
 
+def measure_queries(bt, torch, stream, h: int, text: np.ndarray, m: int = 4 << 20, reps: int = 3) -> dict:
+    """Query throughput of a built tree: m device-resident queries per batch
+    (bt_query_batch), each kind timed with CUDA events over `reps` batches
+    after one warm-up; the arguments are seeded and uniform (access: i in
+    [0, n); rank: a present symbol and i in [0, n]; select: a present symbol
+    and j in [1, its count]).  The first 1000 access answers are checked
+    against the text."""
+    rng = np.random.default_rng(0xB7EE0005)
+    n = len(text)
+    counts = np.bincount(text, minlength=256)
+    syms = np.flatnonzero(counts)
+    c = syms[rng.integers(0, len(syms), m)].astype(np.uint64)
+    args = {
+        bt.BT_Q_ACCESS: rng.integers(0, n, m, dtype=np.uint64),
+        bt.BT_Q_RANK: np.stack([c, rng.integers(0, n + 1, m, dtype=np.uint64)], 1).ravel(),
+        bt.BT_Q_SELECT: np.stack([c, (rng.random(m) * counts[c.astype(np.int64)]).astype(np.uint64) + 1],
+                                 1).ravel(),
+    }
+    out = torch.empty(m, dtype=torch.int64, device="cuda")
+    res = {"queries_per_batch": m, "batches": reps, "args": "seeded uniform, device-resident"}
+    for kind, name in ((bt.BT_Q_ACCESS, "access"), (bt.BT_Q_RANK, "rank"), (bt.BT_Q_SELECT, "select")):
+        d_args = torch.from_numpy(args[kind].view(np.int64)).cuda()
+        bt.bt_query_batch(h, kind, d_args, m, out, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            bt.bt_query_batch(h, kind, d_args, m, out, stream)
+        e1.record(stream)
+        e1.synchronize()
+        res[f"{name}_per_s"] = m * reps / (e0.elapsed_time(e1) / 1e3)
+        if kind == bt.BT_Q_ACCESS:
+            got = out[:1000].cpu().numpy()
+            idx = args[kind][:1000].astype(np.int64)
+            res["access_check"] = bool(np.array_equal(got, text[idx].astype(np.int64)))
+    return res
+
+
 def int_roofline(bt, torch, stream, mulmods_per_step: int, step_ms: float) -> dict:
     """The integer-pipe roofline of the build: the measured rate of the 61-bit
     modular multiply (the library's microbenchmark, one CTA of 256 threads
@@ -423,6 +460,7 @@ def run_ours(args):
     stats = bt.bt_stats(h)
     tree_bytes = bt.bt_device_bytes(h)
     blob = bt.bt_export(h)
+    queries = measure_queries(bt, torch, stream, h, text) if rank == 0 else None
     bt.bt_free(h)
     pinned = torch.from_numpy(text).pin_memory()
     barrier()
@@ -495,6 +533,7 @@ def run_ours(args):
         "roofline": roofline,
         "build_roofline": build_roofline,
         "int_roofline": int_roof,
+        "queries": queries,
         "kernels_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n,
                 "d2h_bytes_per_step": d2h},
