@@ -277,8 +277,8 @@ def measure_queries(bt, torch, stream, h: int, text: np.ndarray, m: int = 4 << 2
 
 def int_roofline(bt, torch, stream, mulmods_per_step: int, step_ms: float) -> dict:
     """The integer-pipe roofline of the build: the measured rate of the 61-bit
-    modular multiply (the library's microbenchmark, one CTA of 256 threads
-    per SM slot, 8 independent chains per thread) against the algorithmic
+    modular multiply (the library's microbenchmark, 8 CTAs of 256 threads per
+    SM, 8 independent chains per thread) against the algorithmic
     multiplies of a step (one per window and length: 2 x the covered bytes)."""
     blocks = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count * 8
     out = torch.empty(blocks * 256, dtype=torch.int64, device="cuda")
