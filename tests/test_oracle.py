@@ -148,6 +148,28 @@ def test_closed_form_unary_text():
         assert p.leaf_text == b"a" * (2 * leaf)
 
 
+def test_closed_form_periodic_text():
+    # T = w^m (truncated to n) with |w| dividing leaf_len: every block, pair
+    # and tail starts at a multiple of |w|, so its string is a prefix of T and
+    # its leftmost occurrence is 0 -- as for a^n.  Marks and pointers (pruned
+    # or not) equal those of a^n of the same length; the leaf text is the
+    # marked last-level blocks of T.
+    rng = random.Random(5)
+    for it in range(40):
+        leaf = rng.choice([2, 4, 6, 8])
+        period = rng.choice([d for d in range(1, leaf + 1) if leaf % d == 0])
+        tau = rng.choice([2, 3, 4])
+        n = rng.randrange(1, 4000)
+        w = bytes(rng.randrange(256) for _ in range(period))
+        text = (w * (n // period + 1))[:n]
+        for prune in (False, True):
+            got = oracle.parse(oracle.build(text, tau, leaf, prune=prune).export())
+            unary = oracle.parse(oracle.build(b"a" * n, tau, leaf, prune=prune).export())
+            assert [lv.marks for lv in got.levels] == [lv.marks for lv in unary.levels]
+            assert [lv.ptrs for lv in got.levels] == [lv.ptrs for lv in unary.levels]
+            check_invariants(text, oracle.build(text, tau, leaf, prune=prune).export())
+
+
 def test_closed_form_no_repeats():
     # Without a repeated window of length leaf_len every block string occurs
     # once, every pair is leftmost and the tree is complete: s*tau^(l-1)
