@@ -444,19 +444,23 @@ static int prune(level* lv, uint32_t L) {
 typedef struct {
   uint8_t* buf;
   uint64_t len, cap;
+  int failed; /* an allocation failed: the output is incomplete */
 } out_buf;
 
-static int put(out_buf* o, uint64_t x) {
+static void put(out_buf* o, uint64_t x) {
+  if (o->failed) return;
   if (o->len + 8 > o->cap) {
     uint64_t cap = o->cap ? 2 * o->cap : 4096;
     uint8_t* nb = (uint8_t*)realloc(o->buf, cap);
-    if (!nb) return BTMT_ENOMEM;
+    if (!nb) {
+      o->failed = 1;
+      return;
+    }
     o->buf = nb;
     o->cap = cap;
   }
   memcpy(o->buf + o->len, &x, 8);
   o->len += 8;
-  return BTMT_OK;
 }
 
 int btmt_build(const uint8_t* T, uint64_t n, uint32_t tau, uint32_t leaf, int do_prune, uint64_t seed,
@@ -494,7 +498,7 @@ int btmt_build(const uint8_t* T, uint64_t n, uint32_t tau, uint32_t leaf, int do
     if (rc == BTMT_OK && l + 1 < L) rc = children(&lv[l], &lv[l + 1]);
   }
   if (rc == BTMT_OK && do_prune) rc = prune(lv, L);
-  out_buf o = {NULL, 0, 0};
+  out_buf o = {NULL, 0, 0, 0};
   if (rc == BTMT_OK) {
     put(&o, 0x31454552544B4C42ull);
     put(&o, n);
@@ -540,7 +544,7 @@ int btmt_build(const uint8_t* T, uint64_t n, uint32_t tau, uint32_t leaf, int do
       }
     }
     if (fill) put(&o, word);
-    if (!o.buf) rc = BTMT_ENOMEM;
+    if (o.failed || !o.buf) rc = BTMT_ENOMEM;
   }
   for (uint32_t l = 0; l < L; l++) level_free(&lv[l]);
   free(lv);
