@@ -116,7 +116,7 @@ int bt_build_ex(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau,
  * identical to the one bt_build_ex makes for that document alone.  On success
  * outs[d] holds document d's tree; if any build fails, every tree of the
  * batch is freed, outs[] is set to NULL and the first failure's status is
- * returned.
+ * returned (BT_ENOMEM when a host worker thread cannot be started).
  */
 int bt_build_batch(const uint8_t* const* texts, const uint64_t* ns, const uint32_t* sigmas,
                    const uint32_t* taus, const uint32_t* leaf_lens, uint64_t ndocs,

@@ -331,7 +331,15 @@ int bt_build_batch(const uint8_t* const* texts, const uint64_t* ns, const uint32
     cudaStreamDestroy(s);
   };
   std::vector<std::thread> pool;
-  for (uint32_t i = 0; i < nworkers; i++) pool.emplace_back(worker);
+  for (uint32_t i = 0; i < nworkers; i++) {
+    try {  // no exception may cross the C ABI: a thread that cannot start ends the batch
+      pool.emplace_back(worker);
+    } catch (...) {
+      int expect = BT_OK;
+      first_error.compare_exchange_strong(expect, BT_ENOMEM);
+      break;
+    }
+  }
   for (auto& th : pool) th.join();
   const int rc = first_error.load();
   if (rc != BT_OK) {
