@@ -275,11 +275,11 @@ def measure_queries(bt, torch, stream, h: int, text: np.ndarray, m: int = 4 << 2
     return res
 
 
-def int_roofline(bt, torch, stream, mulmods_per_step: int, step_ms: float) -> dict:
+def int_roofline(bt, torch, stream, mulmods_per_step: int, step_ms: float, work: str) -> dict:
     """The integer-pipe roofline of the build: the measured rate of the 61-bit
     modular multiply (the library's microbenchmark, 8 CTAs of 256 threads per
-    SM, 8 independent chains per thread) against the algorithmic
-    multiplies of a step (one per window and length: 2 x the covered bytes)."""
+    SM, 8 independent chains per thread) against the 61-bit multiplies the
+    timed kernels actually issue in a step (`work` says how they are counted)."""
     blocks = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count * 8
     out = torch.empty(blocks * 256, dtype=torch.int64, device="cuda")
     bt.bt_mulmod_bench(blocks, 64, out, stream)  # warm-up
@@ -290,10 +290,25 @@ def int_roofline(bt, torch, stream, mulmods_per_step: int, step_ms: float) -> di
     e1.synchronize()
     rate = n / (e0.elapsed_time(e1) / 1e3)
     t_roof_ms = mulmods_per_step / rate * 1e3
-    return {"bound": "alu", "work": "one 61-bit modular multiply per window and length (2 x covered bytes)",
+    return {"bound": "alu", "work": work,
             "mulmods_per_step": mulmods_per_step, "peak": rate / 1e12, "unit": "Tmulmod/s",
             "peak_source": f"measured: {n} multiplies in {e0.elapsed_time(e1):.3f} ms",
             "t_roof_ms": t_roof_ms, "frac": t_roof_ms / step_ms if step_ms > 0 else None}
+
+
+def issued_mulmods(n: int, stats: list[dict]) -> tuple[int, str]:
+    """61-bit modular multiplies a build issues: two per text byte for the
+    prefix fingerprints (the chunk Horner pass and the expansion to every
+    position), one per block for the block fingerprints, one per window the
+    anchored scan tests, and one more per window that matches a block (the
+    fingerprint of the following block for the pair join; an upper bound,
+    since the join is skipped past the slot's last pair start)."""
+    blocks = sum(s["nblocks"] for s in stats)
+    cands = sum(s["candidates"] for s in stats)
+    hits = sum(s["hits"] for s in stats)
+    work = ("issued: 2 per text byte (prefix fingerprints) + 1 per block + 1 per tested window "
+            "+ 1 per window matching a block (pair join, upper bound)")
+    return 2 * n + blocks + cands + hits, work
 
 
 def cpu_mt_baseline(text: np.ndarray, w: dict, sample_mib: int) -> dict:
@@ -505,7 +520,8 @@ def run_ours(args):
         "share_of_step": (scan["ms"] / ms) if ms > 0 else None,
     }
     cov = sum(s["cov"] for s in stats)
-    int_roof = int_roofline(bt, torch, stream, 2 * cov, ms / args.steps)
+    mulmods, mwork = issued_mulmods(n, stats)
+    int_roof = int_roofline(bt, torch, stream, mulmods, ms / args.steps, mwork)
     vbytes = sum(s["verify_bytes"] for s in stats)
     cands = sum(s["candidates"] for s in stats)
     hits = sum(s["hits"] for s in stats)
@@ -518,7 +534,7 @@ def run_ours(args):
                       "frac": (build_gbs / hbm) if (build_gbs and hbm) else None,
                       "frac_of_spec": (build_gbs / HBM_SPEC_GBS) if build_gbs else None,
                       "t_roof_hbm_ms": t_hbm_ms, "t_roof_int_ms": int_roof["t_roof_ms"],
-                      "binding": "int" if int_roof["t_roof_ms"] > t_hbm_ms else "hbm"}
+                      "larger_roof": "int" if int_roof["t_roof_ms"] > t_hbm_ms else "hbm"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,

@@ -44,7 +44,9 @@ typedef enum {
   BT_ERANGE = 2,    /* query out of range; export buffer too small            */
   BT_ENOMEM = 3,    /* device or host allocation failed                       */
   BT_ECUDA = 4,     /* a CUDA call failed (no device, launch error, ...)      */
-  BT_ETIMEOUT = 5,  /* a bounded device-side loop gave up                     */
+  BT_ETIMEOUT = 5,  /* reserved: no entry point returns it today (the library's
+                       kernels wait on nothing that another launch, stream or
+                       device sets, so no device-side wait can run out)       */
   BT_EINTERNAL = 6  /* a device-side invariant check failed                   */
 } bt_status;
 
@@ -197,10 +199,12 @@ int bt_prefix_fingerprints(const uint8_t* d_text, uint64_t n, uint64_t seed, uin
  * GPU that loads the library holds until the process exits.  The entry point
  * calls no cudaMalloc, cudaFree or allocating library routine.
  *  - n may be at most 2^31 (2 GiB); larger texts return BT_ERANGE before any
- *    work is queued.
+ *    other check and before any work is queued.
  *  - The first call on a device looks up the array's device address (with
  *    that device current) and caches it; make that first call before any
- *    stream capture.
+ *    stream capture.  The cache is per device ordinal and is not refreshed
+ *    when the device's primary context is reset (cudaDeviceReset); do not
+ *    call this entry point again in a process after such a reset.
  *  - Every call shares the one array: calls whose work overlaps on the GPU
  *    (for example on two streams) race and give wrong results; serialise
  *    them.  No scratch entry needs to start at zero: each call writes every

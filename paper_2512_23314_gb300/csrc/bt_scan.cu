@@ -337,6 +337,10 @@ constexpr uint64_t kNoAllocMaxN = 1ull << 31;  // largest text accepted (2 GiB)
 constexpr uint64_t kNoAllocAggs = (kNoAllocMaxN / kPrefixStride + kTile - 1) / kTile;
 constexpr uint64_t kNoAllocWords = 2 * (kTile + 1) + kNoAllocAggs;  // 67586 u64, 528 KiB
 constexpr int kNoAllocDevices = 64;
+// The aggregate region holds exactly the CTA totals of the largest text, and
+// the array is the two power tables plus that region.
+static_assert(kNoAllocAggs == 65536, "one aggregate per 1024 chunks of 32 bytes of a 2 GiB text");
+static_assert(kNoAllocWords == 2 * (kTile + 1) + 65536, "power tables + aggregates");
 
 static __device__ __align__(256) uint64_t g_noalloc_scratch[kNoAllocWords];
 
@@ -403,9 +407,9 @@ extern "C" int bt_prefix_fingerprints_noalloc(const uint8_t* d_text, uint64_t n,
                                               uint64_t modulus, uint32_t stride, uint64_t* d_out,
                                               void* stream) {
   using namespace bt;
+  if (n > kNoAllocMaxN) return BT_ERANGE;  // before every other check
   if (!d_text || !d_out || stride != kPrefixStride) return BT_EINVAL;
   if (modulus && (modulus < 300 || modulus >= (1ull << 32))) return BT_EINVAL;
-  if (n > kNoAllocMaxN) return BT_ERANGE;
   uint64_t* scratch = nullptr;
   BT_TRY(noalloc_scratch(&scratch));
   const uint64_t q = modulus ? modulus : Mersenne61::Q;

@@ -44,6 +44,7 @@ class DocResult:
     queried: float = 0.0
     query_batch_s: float = 0.0
     export: bytes | None = None
+    queries: dict | None = None     # kept (arguments, answers) per query kind
 
 
 @dataclass
@@ -69,11 +70,12 @@ class Report:
 
 class Server:
     def __init__(self, hbm_budget: int = 120 << 30, nworkers: int = 8, queries_per_doc: int = 10_000,
-                 keep_exports: bool = False, seed: int = 0):
+                 keep_exports: bool = False, keep_queries: int = 0, seed: int = 0):
         self.budget = hbm_budget
         self.nworkers = nworkers
         self.qpd = queries_per_doc
         self.keep_exports = keep_exports
+        self.keep_queries = keep_queries
         self.seed = seed
         self._lock = threading.Condition()
         self._charged = 0
@@ -99,6 +101,14 @@ class Server:
             self._inflight += 1
             self._max_inflight = max(self._max_inflight, self._inflight)
 
+    def _release(self, estimate: int):
+        """A document whose build or queries failed: its admission charge and
+        its place among the builds in flight are given back."""
+        with self._lock:
+            self._charged -= estimate
+            self._inflight -= 1
+            self._lock.notify_all()
+
     def _retire(self, index: int, handle: int, estimate: int):
         real = bt.bt_device_bytes(handle)
         with self._lock:
@@ -108,28 +118,43 @@ class Server:
             self._lock.notify_all()
 
     # -- queries -----------------------------------------------------------
-    def _queries(self, handle: int, n: int, rng: np.random.Generator, stream) -> float:
-        syms = torch.arange(256, dtype=torch.int64, device="cuda")
-        cnt_args = torch.stack([syms, torch.full_like(syms, n)], 1).reshape(-1).contiguous()
-        counts = torch.empty(256, dtype=torch.int64, device="cuda")
+    def _queries(self, handle: int, n: int, rng: np.random.Generator, stream,
+                 keep: int = 0) -> tuple[float, dict | None]:
+        """One batch of mixed queries on a resident tree, all on `stream` (the
+        argument tensors are made inside the stream context, so no kernel of
+        another stream writes them).  With keep > 0 the first `keep`
+        arguments and answers of each kind are returned for checking."""
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
+            syms = torch.arange(256, dtype=torch.int64, device="cuda")
+            cnt_args = torch.stack([syms, torch.full_like(syms, n)], 1).reshape(-1).contiguous()
+            counts = torch.empty(256, dtype=torch.int64, device="cuda")
             bt.bt_query_batch(handle, bt.BT_Q_RANK, cnt_args, 256, counts, stream)
             c = counts.cpu().numpy()
             present = np.flatnonzero(c > 0)
             q = self.qpd // 3
-            acc = torch.from_numpy(rng.integers(0, n, q)).to("cuda", non_blocking=True)
+            acc_h = rng.integers(0, n, q)
             cs = rng.choice(present, q)
-            rk = torch.from_numpy(np.stack([cs, rng.integers(0, n + 1, q)], 1).reshape(-1)).cuda()
+            rk_h = np.stack([cs, rng.integers(0, n + 1, q)], 1).reshape(-1)
             cs2 = rng.choice(present, q)
             js = (rng.random(q) * c[cs2]).astype(np.int64) + 1
-            sl = torch.from_numpy(np.stack([cs2, js], 1).reshape(-1)).cuda()
+            sl_h = np.stack([cs2, js], 1).reshape(-1)
+            acc = torch.from_numpy(acc_h).to("cuda", non_blocking=True)
+            rk = torch.from_numpy(rk_h).cuda()
+            sl = torch.from_numpy(sl_h).cuda()
             out = torch.empty(3 * q, dtype=torch.int64, device="cuda")
             bt.bt_query_batch(handle, bt.BT_Q_ACCESS, acc, q, out[:q], stream)
             bt.bt_query_batch(handle, bt.BT_Q_RANK, rk, q, out[q:2 * q], stream)
             bt.bt_query_batch(handle, bt.BT_Q_SELECT, sl, q, out[2 * q:], stream)
-            out.cpu()
-        return time.perf_counter() - t0
+            res = out.cpu().numpy()
+        dt = time.perf_counter() - t0
+        kept = None
+        if keep:
+            k = min(keep, q)
+            kept = {"access": (acc_h[:k].copy(), res[:k].copy()),
+                    "rank": (rk_h[:2 * k].reshape(-1, 2).copy(), res[q:q + k].copy()),
+                    "select": (sl_h[:2 * k].reshape(-1, 2).copy(), res[2 * q:2 * q + k].copy())}
+        return dt, kept
 
     # -- main loop ---------------------------------------------------------
     def run(self, arrivals: list[Arrival]) -> Report:
@@ -140,6 +165,37 @@ class Server:
         t_start = time.perf_counter()
         n_total = len(arrivals)
         finished = [0]
+
+        errors = []
+
+        def finish_one():
+            with qlock:
+                finished[0] += 1
+                if finished[0] == n_total:
+                    done.set()
+                qlock.notify_all()
+
+        def serve_one(i, stream, rng, opts):
+            a = arrivals[i]
+            r = results[i]
+            est = estimate_bytes(r.n)
+            self._admit(est)
+            h = None
+            try:
+                r.start = time.perf_counter() - t_start
+                h = bt.bt_build_ex(a.doc.text, r.n, a.doc.sigma, a.doc.tau, a.doc.leaf_len, opts,
+                                   stream.cuda_stream)
+                r.built = time.perf_counter() - t_start
+                if self.keep_exports:
+                    r.export = bt.bt_export(h)
+                r.query_batch_s, r.queries = self._queries(h, r.n, rng, stream, self.keep_queries)
+                r.queried = time.perf_counter() - t_start
+            except BaseException:
+                if h is not None:
+                    bt.bt_free(h)
+                self._release(est)
+                raise
+            self._retire(i, h, est)
 
         def worker(widx: int):
             stream = torch.cuda.Stream()
@@ -152,24 +208,13 @@ class Server:
                     if not pending:
                         return
                     i = pending.popleft()
-                a = arrivals[i]
-                r = results[i]
-                est = estimate_bytes(r.n)
-                self._admit(est)
-                r.start = time.perf_counter() - t_start
-                h = bt.bt_build_ex(a.doc.text, r.n, a.doc.sigma, a.doc.tau, a.doc.leaf_len, opts,
-                                   stream.cuda_stream)
-                r.built = time.perf_counter() - t_start
-                if self.keep_exports:
-                    r.export = bt.bt_export(h)
-                r.query_batch_s = self._queries(h, r.n, rng, stream)
-                r.queried = time.perf_counter() - t_start
-                self._retire(i, h, est)
-                with qlock:
-                    finished[0] += 1
-                    if finished[0] == n_total:
-                        done.set()
-                        qlock.notify_all()
+                try:
+                    serve_one(i, stream, rng, opts)
+                except BaseException as e:  # recorded; run() re-raises the first one
+                    with qlock:
+                        errors.append(e)
+                finally:
+                    finish_one()
 
         threads = [threading.Thread(target=worker, args=(w,), daemon=True) for w in range(self.nworkers)]
         for th in threads:
@@ -191,6 +236,8 @@ class Server:
             th.join()
         wall = time.perf_counter() - t_start
         torch.cuda.synchronize()
+        if errors:
+            raise errors[0]
         build_lat = np.array([r.built - r.arrival for r in results]) * 1e3
         q_lat = np.array([r.query_batch_s for r in results]) * 1e3
         total_bytes = sum(r.n for r in results)

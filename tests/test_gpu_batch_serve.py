@@ -23,6 +23,17 @@ def alone(doc):
     return blob
 
 
+def check_answers(T, kept):
+    """Served query answers against naive counts on the host text: access is
+    T[i], rank counts c in T[0, i), select is the position of the j-th c."""
+    i, got = kept["access"]
+    assert np.array_equal(got, T[i].astype(np.int64))
+    for (c, i), got in zip(*kept["rank"]):
+        assert got == np.count_nonzero(T[:i] == c)
+    for (c, j), got in zip(*kept["select"]):
+        assert got == np.flatnonzero(T == c)[j - 1]
+
+
 def test_batch_equals_standalone_and_oracle():
     docs = workloads.doc_mix(40, min_len=1 << 10, max_len=300 << 10, leaf_len=16, seed=77)
     handles = bt.bt_build_batch([d.text for d in docs], [len(d.text) for d in docs],
@@ -53,7 +64,8 @@ def test_served_results_equal_standalone():
     arrivals = workloads.serve_arrivals(rate=2000.0, duration=0.03, min_len=1 << 10,
                                         max_len=256 << 10, seed=5)
     assert len(arrivals) > 20
-    srv = serve.Server(hbm_budget=256 << 20, nworkers=6, queries_per_doc=300, keep_exports=True)
+    srv = serve.Server(hbm_budget=256 << 20, nworkers=6, queries_per_doc=300, keep_exports=True,
+                       keep_queries=40)
     rep = srv.run(arrivals)
     srv.close()
     assert rep.docs == len(arrivals)
@@ -61,6 +73,7 @@ def test_served_results_equal_standalone():
     for i, (a, r) in enumerate(zip(arrivals, rep.results)):
         assert r.export == alone(a.doc)
         assert r.built >= r.arrival and r.queried >= r.built
+        check_answers(a.doc.text, r.queries)
         if len(a.doc.text) <= 64 << 10 or i % 10 == 0:  # oracle parity on a seeded sample
             ref = oracle.build(a.doc.text, a.doc.tau, a.doc.leaf_len, prune=True).export()
             assert r.export == ref

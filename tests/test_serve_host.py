@@ -56,3 +56,55 @@ def test_admission_waits_for_builds_in_flight(fake_lib):
     s._retire(0, "h0", 80)  # the first build is charged its real 10 bytes
     th.join(timeout=5)
     assert done.is_set() and s._charged == 60 and s._max_inflight == 1
+
+
+class _FakeStream:
+    cuda_stream = 0
+
+
+def _arrivals(k):
+    from paper_2512_23314_gb300.workloads import Arrival, Doc
+    import numpy as np
+    return [Arrival(0.0, Doc(np.zeros(64 + i, np.uint8), 4, 2, 16)) for i in range(k)]
+
+
+def test_worker_error_is_raised_and_releases_its_charge(fake_lib, monkeypatch):
+    """A build that fails in a worker thread ends run() with that error (no
+    hang), and the failed document's admission charge is given back."""
+    monkeypatch.setattr(serve.torch.cuda, "Stream", _FakeStream)
+    monkeypatch.setattr(serve.torch.cuda, "synchronize", lambda *a: None)
+    monkeypatch.setattr(serve.bt, "bt_opts_default", lambda: None)
+    built = []
+
+    def fake_build(text, n, sigma, tau, leaf, opts, stream):
+        if n == 66:
+            raise serve.bt.BTError(serve.bt.BT_EINVAL, "bt_build_ex")
+        built.append(n)
+        return f"h{n}"
+
+    monkeypatch.setattr(serve.bt, "bt_build_ex", fake_build)
+    monkeypatch.setattr(serve.Server, "_queries", lambda self, h, n, rng, stream, keep=0: (0.0, None))
+    s = serve.Server(hbm_budget=1 << 40, nworkers=3)
+    t0 = time.perf_counter()
+    with pytest.raises(serve.bt.BTError):
+        s.run(_arrivals(6))
+    assert time.perf_counter() - t0 < 10
+    assert sorted(built) == [64, 65, 67, 68, 69]
+    assert s._inflight == 0
+    # Only the five built trees stay charged (10 bytes each from the fake).
+    assert s._charged == 50 and len(s._resident) == 5
+
+
+def test_every_worker_failing_still_returns(fake_lib, monkeypatch):
+    monkeypatch.setattr(serve.torch.cuda, "Stream", _FakeStream)
+    monkeypatch.setattr(serve.torch.cuda, "synchronize", lambda *a: None)
+    monkeypatch.setattr(serve.bt, "bt_opts_default", lambda: None)
+
+    def fail(*a):
+        raise RuntimeError("device lost")
+
+    monkeypatch.setattr(serve.bt, "bt_build_ex", fail)
+    s = serve.Server(hbm_budget=1 << 40, nworkers=2)
+    with pytest.raises(RuntimeError, match="device lost"):
+        s.run(_arrivals(5))
+    assert s._inflight == 0 and s._charged == 0
