@@ -90,7 +90,11 @@ typedef struct {
  * about a third fewer windows); where most grams also carry a key first seen
  * late (edits in every copy of a versioned text) few windows are saved and the
  * two extra kernels and the second hit pass cost more, hence off by default. */
-enum { BT_FLAG_DENSE_SCAN = 1, BT_FLAG_TINY_QUEUE = 2, BT_FLAG_GRAM_LIST = 4, BT_FLAG_TWO_PHASE = 8 };
+/* BT_FLAG_BATCH_WORKERS makes bt_build_batch build every document with
+ * bt_build_ex on host worker threads instead of the persistent batched kernel
+ * (the comparison arm of the batched build; the same trees). */
+enum { BT_FLAG_DENSE_SCAN = 1, BT_FLAG_TINY_QUEUE = 2, BT_FLAG_GRAM_LIST = 4, BT_FLAG_TWO_PHASE = 8,
+       BT_FLAG_BATCH_WORKERS = 16 };
 
 void bt_opts_default(bt_opts* opts);
 
@@ -111,18 +115,42 @@ int bt_build_ex(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau,
 /*
  * Build the trees of ndocs independent texts in one call.  Document d is
  * texts[d][0, ns[d]) with sigmas[d], taus[d], leaf_lens[d]; every document
- * uses *opts (NULL: defaults).  Texts may be host or device pointers.  The
- * documents are distributed over `nworkers` host workers (0: 8), each issuing
- * its builds on its own CUDA stream, so the small kernels and per-level
- * synchronisations of different documents overlap on the GPU.  Each tree is
- * identical to the one bt_build_ex makes for that document alone.  On success
- * outs[d] holds document d's tree; if any build fails, every tree of the
- * batch is freed, outs[] is set to NULL and the first failure's status is
- * returned (BT_ENOMEM when a host worker thread cannot be started).
+ * uses *opts (NULL: defaults).  Texts may be host or device pointers.
+ *
+ * Documents of at most 2^30 bytes and 40 levels are built by one persistent
+ * kernel launch per size class (the paper's section 3 levels and section 3.1
+ * pass, per document): each CTA takes the next document from a device work
+ * queue (longest first) and builds its whole tree -- alphabet, prefix
+ * fingerprints, every level's scan, verification, marks, pointers and split,
+ * pruning and counters -- level by level with barriers of the CTA, without
+ * any host round trip.  The trees of one call share one device allocation,
+ * released when the last of them is freed.  Larger documents, and every
+ * document when opts->flags has BT_FLAG_BATCH_WORKERS, are built with
+ * bt_build_ex on `nworkers` host threads (0: 8), one CUDA stream each.
+ *
+ * Each tree is identical to the one bt_build_ex makes for that document
+ * alone.  On success outs[d] holds document d's tree; if any build fails,
+ * every tree of the batch is freed, outs[] is set to NULL and the first
+ * failure's status is returned (BT_EINVAL for bad arguments, including a
+ * document with more distinct bytes than its sigma; BT_ENOMEM when device
+ * memory or a host worker thread is not available).
  */
 int bt_build_batch(const uint8_t* const* texts, const uint64_t* ns, const uint32_t* sigmas,
                    const uint32_t* taus, const uint32_t* leaf_lens, uint64_t ndocs,
                    const bt_opts* opts, uint32_t nworkers, bt_tree** outs);
+
+/* Measurement hooks of the batched build (not part of the paper's method).
+ * bt_batch_report: what the last bt_build_batch call of the process did, 9
+ * u64: documents built by the batched kernel, documents built by host
+ * workers, kernel launches, documents built a second time because the output
+ * pool ran out, threads per CTA, CTAs per SM, output pool bytes, CTA scratch
+ * bytes, the largest grid.  bt_batch_cycles: for a tree from the batched
+ * kernel, the SM clock cycles its CTA spent per phase (6 u64: set-up,
+ * tables, window scan, verification/marks/pointers/split, pruning, output
+ * and counters); zeros for other trees.  BT_EINVAL for null pointers or cap
+ * too small. */
+int bt_batch_report(uint64_t* out, uint32_t cap);
+int bt_batch_cycles(const bt_tree* t, uint64_t* out, uint32_t cap);
 
 /* access(i) = T[i], 0 <= i < n (section 1).  BT_ERANGE if i >= n. */
 int bt_access(const bt_tree* t, uint64_t i, uint8_t* out);

@@ -23,6 +23,7 @@ BT_FLAG_DENSE_SCAN = 1
 BT_FLAG_TINY_QUEUE = 2
 BT_FLAG_GRAM_LIST = 4
 BT_FLAG_TWO_PHASE = 8
+BT_FLAG_BATCH_WORKERS = 16
 ST_FIELDS = 10
 ST_NAMES = ("nblocks", "b", "cov", "nmarked", "npairs", "verify_bytes", "collisions",
             "final_blocks", "candidates", "hits")
@@ -86,6 +87,8 @@ def lib() -> ctypes.CDLL:
     L.bt_launch_count.argtypes = []
     L.bt_launch_count.restype = u64
     L.bt_mulmod_bench.argtypes = [u32, u32, u64, vp, vp, P(u64)]
+    L.bt_batch_report.argtypes = [vp, u32]
+    L.bt_batch_cycles.argtypes = [vp, vp, u32]
     for name in ("bt_profile_read", "bt_build", "bt_build_ex", "bt_build_batch", "bt_access", "bt_rank", "bt_select",
                  "bt_query_batch", "bt_export", "bt_stats", "bt_prefix_fingerprints",
                  "bt_prefix_fingerprints_noalloc", "bt_mulmod_bench"):
@@ -173,6 +176,22 @@ def bt_build_batch(texts, ns, sigmas, taus, leaf_lens, opts: bt_opts | None = No
            "bt_build_batch")
     del keep
     return [outs[i] for i in range(nd)]
+
+
+def bt_batch_report() -> dict:
+    """What the last bt_build_batch call did (measurement hook)."""
+    a = (ctypes.c_uint64 * 9)()
+    _check(lib().bt_batch_report(a, 9), "bt_batch_report")
+    names = ("kernel_docs", "worker_docs", "launches", "retried", "threads", "ctas_per_sm", "pool_bytes",
+             "scratch_bytes", "max_grid")
+    return dict(zip(names, list(a)))
+
+
+def bt_batch_cycles(t: int) -> list[int]:
+    """SM cycles per phase of the CTA that built a batched tree."""
+    a = (ctypes.c_uint64 * 6)()
+    _check(lib().bt_batch_cycles(t, a, 6), "bt_batch_cycles")
+    return list(a)
 
 
 def bt_access(t: int, i: int) -> int:
@@ -296,6 +315,7 @@ class BuildOptions:
     tiny_queue: bool = False  # test hook: forces the scan's queue-overflow path
     gram_list: bool = False  # test hook: selected-gram list whatever the text length
     two_phase: bool = False  # two-phase window tests on every anchored level (same tree)
+    batch_workers: bool = False  # bt_build_batch: host workers instead of the batched kernel
 
     def to_c(self):
         o = bt_opts_default()
@@ -307,7 +327,8 @@ class BuildOptions:
         o.flags = ((BT_FLAG_DENSE_SCAN if self.dense_scan else 0)
                    | (BT_FLAG_TINY_QUEUE if self.tiny_queue else 0)
                    | (BT_FLAG_GRAM_LIST if self.gram_list else 0)
-                   | (BT_FLAG_TWO_PHASE if self.two_phase else 0))
+                   | (BT_FLAG_TWO_PHASE if self.two_phase else 0)
+                   | (BT_FLAG_BATCH_WORKERS if self.batch_workers else 0))
         keep = None
         if self.level_sizes is not None:
             keep = np.ascontiguousarray(self.level_sizes, dtype=np.uint64)

@@ -21,6 +21,13 @@ namespace bt {
 
 int alphabet(const uint8_t* T, uint64_t n, uint32_t sigma, bt_tree* t, cudaStream_t s);
 int upload_view(bt_tree* t, cudaStream_t s);
+int batch_kernel_build(const uint8_t* const* texts, const uint64_t* ns, const uint32_t* sigmas,
+                       const uint32_t* taus, const uint32_t* leaf_lens, uint64_t ndocs, const bt_opts& o,
+                       std::vector<char>& routed, bt_tree** outs, uint32_t threads, uint32_t ctas_per_sm,
+                       cudaStream_t s);
+void batch_config(const uint64_t* ns, uint64_t ndocs, uint32_t* threads, uint32_t* ctas_per_sm);
+void batch_report_workers(uint64_t docs);
+void batch_report_reset();
 int run_queries(const bt_tree* t, int kind, const uint64_t* d_args, uint64_t m, uint64_t* d_out,
                 cudaStream_t s);
 
@@ -73,12 +80,30 @@ static uint64_t splitmix(uint64_t x) {
   return x ^ (x >> 31);
 }
 
-static uint64_t base_for(uint64_t seed, uint64_t q) { return splitmix(seed) % (q - 256) + 256; }
+uint64_t base_for(uint64_t seed, uint64_t q) { return splitmix(seed) % (q - 256) + 256; }
+
+// Streaming multiprocessors of the current device (cached per device).
+unsigned device_sm_count() {
+  static std::atomic<unsigned> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 152;
+  }
+  unsigned v = cache[dev].load(std::memory_order_relaxed);
+  if (v) return v;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    n = 152;
+  }
+  cache[dev].store((unsigned)n, std::memory_order_relaxed);
+  return (unsigned)n;
+}
 
 // Block sizes: b_L = leaf_len, b_l = tau * b_{l+1}, height the smallest h
 // with s0 * leaf_len * tau^h >= n (section 3 assumes n = s * tau^h).
-static int plan_sizes(uint64_t n, uint32_t tau, uint32_t leaf, const bt_opts& o,
-                      std::vector<uint64_t>& b) {
+int plan_sizes(uint64_t n, uint32_t tau, uint32_t leaf, const bt_opts& o, std::vector<uint64_t>& b) {
   b.clear();
   if (o.level_sizes) {
     if (o.nlevels == 0 || o.nlevels > kMaxLevels) return BT_EINVAL;
@@ -113,6 +138,10 @@ static void free_tree_memory(bt_tree* t) {
     for (void* a : v.owned)
       if (a) cudaFreeAsync(a, s);
     v.owned.clear();
+  }
+  if (t->slab) {  // a batched tree: its arrays belong to the batch's pool
+    t->slab.reset();
+    return;
   }
   void* rest[] = {t->leaf, t->pre, t->sym, t->view};
   for (void* a : rest)
@@ -250,6 +279,59 @@ static cudaStream_t as_stream(void* s) { return s ? (cudaStream_t)s : cudaStream
 
 
 
+
+// Documents not routed to the batched kernel: host workers, each issuing
+// bt_build_ex on its own CUDA stream.
+static int worker_builds(const uint8_t* const* texts, const uint64_t* ns, const uint32_t* sigmas,
+                         const uint32_t* taus, const uint32_t* leaf_lens, uint64_t ndocs, const bt_opts* opts,
+                         uint32_t nworkers, const std::vector<char>& routed, bt_tree** outs) {
+  std::vector<uint64_t> todo;
+  for (uint64_t d = 0; d < ndocs; d++)
+    if (!routed[d]) todo.push_back(d);
+  if (todo.empty()) return BT_OK;
+  if (nworkers == 0) nworkers = 8;
+  if (nworkers > todo.size()) nworkers = (uint32_t)todo.size();
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) {
+    cudaGetLastError();
+    return BT_ECUDA;
+  }
+  std::atomic<uint64_t> next{0};
+  std::atomic<int> first_error{BT_OK};
+  auto worker = [&]() {
+    cudaSetDevice(device);
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      int expect = BT_OK;
+      first_error.compare_exchange_strong(expect, BT_ECUDA);
+      return;
+    }
+    for (;;) {
+      const uint64_t j = next.fetch_add(1);
+      if (j >= todo.size() || first_error.load() != BT_OK) break;
+      const uint64_t d = todo[j];
+      const int rc = bt_build_ex(texts[d], ns[d], sigmas[d], taus[d], leaf_lens[d], opts, s, &outs[d]);
+      if (rc != BT_OK) {
+        int expect = BT_OK;
+        first_error.compare_exchange_strong(expect, rc);
+      }
+    }
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  };
+  std::vector<std::thread> pool;
+  for (uint32_t i = 0; i < nworkers; i++) {
+    try {  // no exception may cross the C ABI: a thread that cannot start ends the batch
+      pool.emplace_back(worker);
+    } catch (...) {
+      int expect = BT_OK;
+      first_error.compare_exchange_strong(expect, BT_ENOMEM);
+      break;
+    }
+  }
+  for (auto& th : pool) th.join();
+  return first_error.load();
+}
 }  // namespace bt
 
 using namespace bt;
@@ -301,47 +383,37 @@ int bt_build_batch(const uint8_t* const* texts, const uint64_t* ns, const uint32
   if (!outs || (ndocs && (!texts || !ns || !sigmas || !taus || !leaf_lens))) return BT_EINVAL;
   for (uint64_t d = 0; d < ndocs; d++) outs[d] = nullptr;
   if (ndocs == 0) return BT_OK;
-  if (nworkers == 0) nworkers = 8;
-  if (nworkers > ndocs) nworkers = (uint32_t)ndocs;
-  int device = 0;
-  if (cudaGetDevice(&device) != cudaSuccess) {
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();
     return BT_ECUDA;
   }
-  std::atomic<uint64_t> next{0};
-  std::atomic<int> first_error{BT_OK};
-  auto worker = [&]() {
-    cudaSetDevice(device);
+  bt_opts o;
+  if (opts) o = *opts;
+  else bt_opts_default(&o);
+  // The persistent batched kernel takes every document it can; the rest (and
+  // every document with BT_FLAG_BATCH_WORKERS) go to host workers.
+  std::vector<char> routed(ndocs, 0);
+  int rc = BT_OK;
+  batch_report_reset();
+  if (!(o.flags & BT_FLAG_BATCH_WORKERS)) {
     cudaStream_t s;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-      int expect = BT_OK;
-      first_error.compare_exchange_strong(expect, BT_ECUDA);
-      return;
+      cudaGetLastError();
+      return BT_ECUDA;
     }
-    for (;;) {
-      const uint64_t d = next.fetch_add(1);
-      if (d >= ndocs || first_error.load() != BT_OK) break;
-      const int rc = bt_build_ex(texts[d], ns[d], sigmas[d], taus[d], leaf_lens[d], opts, s, &outs[d]);
-      if (rc != BT_OK) {
-        int expect = BT_OK;
-        first_error.compare_exchange_strong(expect, rc);
-      }
-    }
+    uint32_t threads = 0, ctas = 0;
+    batch_config(ns, ndocs, &threads, &ctas);
+    rc = batch_kernel_build(texts, ns, sigmas, taus, leaf_lens, ndocs, o, routed, outs, threads, ctas, s);
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
-  };
-  std::vector<std::thread> pool;
-  for (uint32_t i = 0; i < nworkers; i++) {
-    try {  // no exception may cross the C ABI: a thread that cannot start ends the batch
-      pool.emplace_back(worker);
-    } catch (...) {
-      int expect = BT_OK;
-      first_error.compare_exchange_strong(expect, BT_ENOMEM);
-      break;
-    }
   }
-  for (auto& th : pool) th.join();
-  const int rc = first_error.load();
+  if (rc == BT_OK) {
+    uint64_t nw = 0;
+    for (uint64_t d = 0; d < ndocs; d++) nw += !routed[d];
+    batch_report_workers(nw);
+    rc = worker_builds(texts, ns, sigmas, taus, leaf_lens, ndocs, opts, nworkers, routed, outs);
+  }
   if (rc != BT_OK) {
     for (uint64_t d = 0; d < ndocs; d++) {
       bt_free(outs[d]);

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -141,7 +142,7 @@ struct LevelView {
 
 // Bytes per symbol counter of a level with block length b: a count never
 // exceeds b.
-inline uint32_t counter_width(uint64_t b) { return b <= 0xFF ? 1 : b <= 0xFFFF ? 2 : 4; }
+__host__ __device__ inline uint32_t counter_width(uint64_t b) { return b <= 0xFF ? 1 : b <= 0xFFFF ? 2 : 4; }
 
 // Counter i of a row array with w-byte entries.
 __device__ __forceinline__ uint32_t cget(const void* a, uint32_t w, uint64_t i) {
@@ -181,6 +182,11 @@ struct bt_tree {
   bt::TreeView* view = nullptr;  // device copy of the view
   int device = 0;
   uint64_t dev_bytes = 0;        // device memory held by the tree
+  // Trees of a batched build live in a region of the batch's output pool:
+  // the pool is released when the last of its trees is freed, and the
+  // arrays above are not freed one by one.
+  std::shared_ptr<void> slab;
+  uint64_t batch_cycles[6] = {};  // batched build: SM cycles per phase of its CTA
 };
 
 namespace bt {
