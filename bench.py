@@ -76,10 +76,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-build and serving measurements")
-    ap.add_argument("--batch-docs", type=int, default=512,
-                    help="documents of the batched-build measurement (8192: the full batched workload)")
-    ap.add_argument("--batch-max-mib", type=int, default=1,
-                    help="largest document of the batched-build measurement in MiB (16: the full workload)")
+    ap.add_argument("--batch-docs", type=int, default=8192,
+                    help="documents of the batched-build measurement (default: the full batched workload)")
+    ap.add_argument("--batch-max-mib", type=int, default=16,
+                    help="largest document of the batched-build measurement in MiB")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched-build measurement and print its JSON object")
     ap.add_argument("--summarize-launches", metavar="CSV",
@@ -328,11 +328,18 @@ def cpu_mt_baseline(text: np.ndarray, w: dict, sample_mib: int) -> dict:
                       f"one OpenMP build on {cpu_mt.threads()} threads"}
 
 
-def measure_batch(ndocs: int = 512, min_len: int = 4 << 10, max_len: int = 1 << 20,
+def measure_batch(ndocs: int = 8192, min_len: int = 4 << 10, max_len: int = 16 << 20,
                   nworkers: int = 16) -> dict:
-    """Many small documents (the batched workload scaled down): one document
-    per bt_build_ex call, back to back, against one bt_build_batch call.
-    Texts start in host memory in both arms; trees are freed after timing."""
+    """The batched workload: `ndocs` versioned-text documents of log-uniform
+    length (4 KiB - 16 MiB by default: 8192 documents, ~16.5 GB), sigma
+    4-128, tau 2/4/8, leaf 32.  Three arms, texts in host memory in each:
+      plain   -- one bt_build_ex call per document, back to back (one
+                 document per launch sequence);
+      workers -- bt_build_batch with BT_FLAG_BATCH_WORKERS (bt_build_ex on
+                 host threads, one CUDA stream each);
+      kernel  -- bt_build_batch: the persistent batched kernel.
+    Each arm is timed once after a warm-up batch; the exports of a seeded
+    sample of documents are compared between the arms."""
     import torch
 
     from paper_2512_23314_gb300 import bt
@@ -341,48 +348,76 @@ def measure_batch(ndocs: int = 512, min_len: int = 4 << 10, max_len: int = 1 << 
     gen_s = time.perf_counter() - t_gen
     args = ([d.text for d in docs], [len(d.text) for d in docs], [d.sigma for d in docs],
             [d.tau for d in docs], [d.leaf_len for d in docs])
-    warm = bt.bt_build_batch(*(a[:16] for a in args), nworkers=nworkers)
+    sample = sorted(np.random.default_rng(7).choice(ndocs, min(64, ndocs), replace=False).tolist())
+    o_kernel, _ = bt.BuildOptions().to_c()
+    o_workers, _ = bt.BuildOptions(batch_workers=True).to_c()
+
+    def batch_arm(o):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hs = bt.bt_build_batch(*args, o, nworkers=nworkers)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        blobs = [hashlib.sha256(bt.bt_export(hs[i])).hexdigest() for i in sample]
+        rep = bt.bt_batch_report()
+        cyc = np.array([bt.bt_batch_cycles(h) for h in hs], dtype=np.float64)
+        for h in hs:
+            bt.bt_free(h)
+        return dt, blobs, rep, cyc
+
+    warm = bt.bt_build_batch(*(a[:64] for a in args), o_kernel, nworkers=nworkers)
     for h in warm:
         bt.bt_free(h)
+    kernel_s, kernel_blobs, rep, cyc = batch_arm(o_kernel)
+    workers_s, workers_blobs, _, _ = batch_arm(o_workers)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    hs = []
-    for d in docs:
-        hs.append(bt.bt_build_ex(d.text, len(d.text), d.sigma, d.tau, d.leaf_len))
+    plain_blobs = {}
+    for i, d in enumerate(docs):
+        h = bt.bt_build_ex(d.text, len(d.text), d.sigma, d.tau, d.leaf_len)
+        if i in sample:
+            plain_blobs[i] = hashlib.sha256(bt.bt_export(h)).hexdigest()
+        bt.bt_free(h)
+    torch.cuda.synchronize()
     plain_s = time.perf_counter() - t0
-    for h in hs:
-        bt.bt_free(h)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    hs = bt.bt_build_batch(*args, nworkers=nworkers)
-    batch_s = time.perf_counter() - t0
-    for h in hs:
-        bt.bt_free(h)
+    same = kernel_blobs == workers_blobs == [plain_blobs[i] for i in sample]
     total = sum(len(d.text) for d in docs)
+    phases = ["setup", "tables", "window_scan", "verify_mark_split", "prune", "output_counters"]
+    share = (cyc.sum(0) / cyc.sum()).tolist() if cyc.sum() > 0 else None
     return {"workload": f"{ndocs} versioned-text documents, log-uniform {min_len >> 10} KiB - "
-                        f"{max_len >> 20} MiB, sigma 4-128, tau 2/4/8, leaf 32",
-            "generate_s": gen_s,
-            "docs": ndocs, "bytes": total, "nworkers": nworkers,
-            "docs_per_s": ndocs / batch_s, "plain_docs_per_s": ndocs / plain_s,
-            "speedup": plain_s / batch_s, "batch_mb_per_s": total / batch_s / 1e6,
-            "plain_mb_per_s": total / plain_s / 1e6}
+                        f"{max_len >> 20} MiB, sigma 4-128, tau 2/4/8, leaf 32; texts in host memory",
+            "generate_s": gen_s, "docs": ndocs, "bytes": total,
+            "docs_per_s": ndocs / kernel_s, "mb_per_s": total / kernel_s / 1e6,
+            "workers_docs_per_s": ndocs / workers_s, "plain_docs_per_s": ndocs / plain_s,
+            "speedup_vs_plain": plain_s / kernel_s, "speedup_vs_workers": workers_s / kernel_s,
+            "workers_mb_per_s": total / workers_s / 1e6, "plain_mb_per_s": total / plain_s / 1e6,
+            "identical_output_sample": {"docs": len(sample), "equal": bool(same)},
+            "kernel": rep, "kernel_phase_share": dict(zip(phases, share)) if share else None,
+            "nworkers": nworkers}
 
 
-def measure_serve(rate: float = 2000.0, duration: float = 0.25, min_len: int = 1 << 10,
-                  max_len: int = 2 << 20, nworkers: int = 16) -> dict:
-    """The serving loop on a scaled-down arrival stream: 0.25 s of Poisson
-    arrivals of documents of 1 KiB - 2 MiB (the full stream offers ~120 GB of
-    text, too much to generate within a bench run)."""
+def measure_serve(rate: float = 2000.0, duration: float = 0.5, min_len: int = 1 << 10,
+                  max_len: int = 64 << 20, lanes: int = 4) -> dict:
+    """The serving loop over the serving workload's full length range (1 KiB -
+    64 MiB, DNA-like / text-like 50/50, 120 GiB budget, 10^4 queries per
+    document), with a 0.5 s window of Poisson arrivals at 2000 documents/s
+    (the 10 s stream would offer ~120 GB of text, too much to generate within
+    a bench run).  Documents up to 4 MiB are built in micro-batches by the
+    batched kernel, larger ones alone."""
     from paper_2512_23314_gb300 import serve
+    t0 = time.perf_counter()
     arrivals = workloads.serve_arrivals(rate=rate, duration=duration, min_len=min_len,
                                         max_len=max_len)
-    srv = serve.Server(hbm_budget=120 << 30, nworkers=nworkers, queries_per_doc=10_000)
+    gen_s = time.perf_counter() - t0
+    srv = serve.Server(hbm_budget=120 << 30, lanes=lanes, queries_per_doc=10_000)
     rep = srv.run(arrivals)
     srv.close()
     out = rep.summary()
-    out["workload"] = (f"Poisson {rate:.0f} docs/s for {duration} s, log-uniform "
+    out["generate_s"] = gen_s
+    out["offered_mb_per_s"] = sum(len(a.doc.text) for a in arrivals) / max(duration, 1e-9) / 1e6
+    out["workload"] = (f"Poisson {rate:.0f} docs/s for {duration} s ({len(arrivals)} documents), log-uniform "
                        f"{min_len >> 10} KiB - {max_len >> 20} MiB, DNA-like / text-like 50/50, "
-                       f"120 GiB budget, {out['queries_per_doc']} queries per document")
+                       f"120 GiB budget, {out['queries_per_doc']} queries per document, {lanes} lanes")
     return out
 
 
@@ -414,6 +449,92 @@ def run_reference(args):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def scan_roofline(prof: dict, step_ms_total: float, traffic_ratio: float | None) -> dict:
+    """Roofline of the window scan from the library's CUDA-event profile:
+    covered bytes of the timed levels / their event time, against the
+    measured HBM copy bandwidth."""
+    hbm = measured_peaks().get("hbm_gbs")
+    scan = prof.get("window_scan", {"launches": 0, "ms": 0.0, "bytes": 0})
+    achieved = scan["bytes"] / (scan["ms"] / 1e3) / 1e9 if scan["ms"] > 0 else None
+    per_launch_bytes = scan["bytes"] / max(1, scan["launches"])
+    return {
+        "kernel": "window scan of a level (k_scan_stream or k_scan_list, k_scan_anchor, k_hits, "
+                  "k_candidates, and the tail-key k_scan)",
+        "bound": "hbm",
+        "achieved": achieved,
+        "peak": hbm if hbm else 6800.0,
+        "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "of fallback",
+        "unit": "GB/s",
+        "frac": (achieved / hbm) if (achieved and hbm) else None,
+        "frac_of_spec": (achieved / HBM_SPEC_GBS) if achieved else None,
+        "traffic": (traffic_ratio * per_launch_bytes) if traffic_ratio is not None else None,
+        "alg_bytes_per_launch": per_launch_bytes,
+        "launches": scan["launches"],
+        "share_of_step": (scan["ms"] / step_ms_total) if step_ms_total > 0 else None,
+    }
+
+
+def measure_single_text(bt, torch, stream, name: str, steps: int, warmup: int) -> dict:
+    """Another single-text workload (the 2 GiB DNA copies by default), timed
+    the same way as the headline: device-resident input, CUDA events over
+    `steps` builds after `warmup`; then end to end from pinned host memory
+    with the export read back."""
+    w = WORKLOADS[name]
+    t0 = time.perf_counter()
+    text = w["gen"]()
+    gen_s = time.perf_counter() - t0
+    n = len(text)
+    d_text = torch.from_numpy(text).cuda()
+    opts = bt.BuildOptions(prune=True, **w.get("opts", {})).to_c()[0]
+
+    def step(src):
+        return bt.bt_build_ex(src, n, w["sigma"], w["tau"], w["leaf"], opts, stream)
+
+    for _ in range(warmup):
+        bt.bt_free(step(d_text))
+    torch.cuda.synchronize()
+    bt.bt_profile_reset()
+    bt.bt_profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        bt.bt_free(step(d_text))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    bt.bt_profile_enable(False)
+    prof = bt.bt_profile_read()
+    ms = e0.elapsed_time(e1)
+    h = step(d_text)
+    stats = bt.bt_stats(h)
+    tree_bytes = bt.bt_device_bytes(h)
+    bt.bt_free(h)
+    del d_text
+    pinned = torch.from_numpy(text).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(steps):
+        h = step(pinned)
+        d2h = len(bt.bt_export(h))
+        bt.bt_free(h)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    hbm = measured_peaks().get("hbm_gbs") or 6800.0
+    cov = sum(s["cov"] for s in stats)
+    alg = n + cov + sum(s["verify_bytes"] for s in stats) + tree_bytes
+    step_ms = ms / steps
+    return {"workload": name, "desc": w["desc"], "n": n, "sigma": w["sigma"], "tau": w["tau"],
+            "leaf_len": w["leaf"], "build_options": w.get("opts", {}), "generate_s": gen_s,
+            "value": throughput_mbs(n, steps, 1, ms), "unit": UNIT, "steps": steps, "warmup": warmup,
+            "ms_per_step": step_ms, "levels": len(stats), "sum_cov_bytes": cov,
+            "roofline": scan_roofline(prof, ms, None),
+            "build_roofline": {"alg_bytes_per_step": alg, "achieved": alg / (step_ms / 1e3) / 1e9,
+                               "peak": hbm, "unit": "GB/s", "frac": alg / (step_ms / 1e3) / 1e9 / hbm},
+            "kernels_ms_per_step": {k: v["ms"] / steps for k, v in prof.items()},
+            "e2e": {"value": throughput_mbs(n, steps, 1, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": n,
+                    "d2h_bytes_per_step": d2h}}
 
 
 def run_ours(args):
@@ -500,25 +621,7 @@ def run_ours(args):
 
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
-    scan = prof.get("window_scan", {"launches": 0, "ms": 0.0, "bytes": 0})
-    achieved = scan["bytes"] / (scan["ms"] / 1e3) / 1e9 if scan["ms"] > 0 else None
-    ratio = recorded_traffic("window_scan")
-    per_launch_bytes = scan["bytes"] / max(1, scan["launches"])
-    roofline = {
-        "kernel": "window scan of a level (k_scan_stream or k_scan_list, k_scan_anchor, k_hits, "
-                  "k_candidates, and the tail-key k_scan)",
-        "bound": "hbm",
-        "achieved": achieved,
-        "peak": hbm if hbm else 6800.0,
-        "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "of fallback",
-        "unit": "GB/s",
-        "frac": (achieved / hbm) if (achieved and hbm) else None,
-        "frac_of_spec": (achieved / HBM_SPEC_GBS) if achieved else None,
-        "traffic": (ratio * per_launch_bytes) if ratio is not None else None,
-        "alg_bytes_per_launch": per_launch_bytes,
-        "launches": scan["launches"],
-        "share_of_step": (scan["ms"] / ms) if ms > 0 else None,
-    }
+    roofline = scan_roofline(prof, ms, recorded_traffic("window_scan"))
     cov = sum(s["cov"] for s in stats)
     mulmods, mwork = issued_mulmods(n, stats)
     int_roof = int_roofline(bt, torch, stream, mulmods, ms / args.steps, mwork)
@@ -557,6 +660,11 @@ def run_ours(args):
         "clocks": clocks,
     }
     if world == 1 and not args.no_extras:
+        # The headline is the 256 MiB versioned text (the workload the metric is
+        # quoted on); the 2 GiB DNA copies, the batched workload and the serving
+        # loop are measured beside it.
+        line["configs"] = {"dna_genome_2GiB": measure_single_text(bt, torch, stream, "dna_genome_2GiB",
+                                                                  steps=3, warmup=2)}
         line["batch"] = measure_batch(args.batch_docs, max_len=args.batch_max_mib << 20)
         line["serve"] = measure_serve()
     if world == 1 and not args.no_cpu_baseline:

@@ -71,6 +71,11 @@ typedef struct {
                                   single-thread right-to-left finish of the
                                   rest; 0 = default 4096.                     */
   uint32_t flags;              /* BT_FLAG_* (0 by default)                    */
+  uint32_t batch_ctas;         /* bt_build_batch: CTAs of the batched kernel's
+                                  launch; 0 (default) = the autotuned shape
+                                  over every SM.  A smaller grid leaves SMs to
+                                  other work, e.g. a second batch on another
+                                  host thread.                                 */
 } bt_opts;
 
 /* flags: BT_FLAG_DENSE_SCAN probes the table at every window position instead

@@ -39,7 +39,8 @@ class bt_opts(ctypes.Structure):
     _fields_ = [("prune", ctypes.c_int), ("root_arity", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("modulus", ctypes.c_uint64),
                 ("level_sizes", ctypes.c_void_p), ("nlevels", ctypes.c_uint32),
-                ("max_rounds", ctypes.c_uint64), ("flags", ctypes.c_uint32)]
+                ("max_rounds", ctypes.c_uint64), ("flags", ctypes.c_uint32),
+                ("batch_ctas", ctypes.c_uint32)]
 
 
 _lib = None
@@ -316,6 +317,7 @@ class BuildOptions:
     gram_list: bool = False  # test hook: selected-gram list whatever the text length
     two_phase: bool = False  # two-phase window tests on every anchored level (same tree)
     batch_workers: bool = False  # bt_build_batch: host workers instead of the batched kernel
+    batch_ctas: int = 0  # bt_build_batch: CTAs of the batched kernel's launch (0: every SM)
 
     def to_c(self):
         o = bt_opts_default()
@@ -324,6 +326,7 @@ class BuildOptions:
         o.seed = self.seed
         o.modulus = self.modulus
         o.max_rounds = self.max_rounds
+        o.batch_ctas = self.batch_ctas
         o.flags = ((BT_FLAG_DENSE_SCAN if self.dense_scan else 0)
                    | (BT_FLAG_TINY_QUEUE if self.tiny_queue else 0)
                    | (BT_FLAG_GRAM_LIST if self.gram_list else 0)

@@ -402,6 +402,9 @@ int bt_build_batch(const uint8_t* const* texts, const uint64_t* ns, const uint32
       cudaGetLastError();
       return BT_ECUDA;
     }
+    int device = 0;
+    if (cudaGetDevice(&device) == cudaSuccess) keep_pool_memory(device);
+    cudaGetLastError();
     uint32_t threads = 0, ctas = 0;
     batch_config(ns, ndocs, &threads, &ctas);
     rc = batch_kernel_build(texts, ns, sigmas, taus, leaf_lens, ndocs, o, routed, outs, threads, ctas, s);

@@ -1447,17 +1447,20 @@ int launch_docs(const M& m, const BParams& base, const std::vector<const DocPlan
   return BT_OK;
 }
 
+// Device memory of one batched call, stream-ordered on the call's stream (no
+// device-wide synchronisation, so calls on several host threads overlap).
 struct DevFree {
+  cudaStream_t s = nullptr;
   std::vector<void*> p;
   ~DevFree() {
-    for (void* q : p) cudaFree(q);
+    for (void* q : p) cudaFreeAsync(q, s);
   }
   template <class T>
   int alloc(T** out, uint64_t count) {
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, (count ? count : 1) * sizeof(T));
+    cudaError_t e = cudaMallocAsync(&q, (count ? count : 1) * sizeof(T), s);
     if (e != cudaSuccess) {
-      note_cuda_error(e, "cudaMalloc", __FILE__, __LINE__);
+      note_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
       cudaGetLastError();
       return e == cudaErrorMemoryAllocation ? BT_ENOMEM : BT_ECUDA;
     }
@@ -1487,6 +1490,7 @@ int run_batch(const M& m, const uint8_t* const* texts, const uint32_t* taus, con
     return a->n * a->L > b->n * b->L;
   });
   DevFree mem;
+  mem.s = s;
   // Texts, each at a 16-byte aligned offset and followed by at least 48 bytes
   // of padding (16-byte loads past a text's end stay in the buffer).
   std::vector<uint64_t> toff(nd);
@@ -1539,14 +1543,20 @@ int run_batch(const M& m, const uint8_t* const* texts, const uint32_t* taus, con
   // size it reported.
   uint64_t pool_cap = 0;
   for (uint64_t k = 0; k < nd; k++) pool_cap += 3 * plans[k].n + (32u << 10);
+  // The pool outlives the call: it is returned to the device's stream-ordered
+  // pool when the last tree is freed (on the freeing thread's stream; a tree
+  // is never freed while queries on it run).
   auto make_pool = [&](uint64_t cap, std::shared_ptr<void>& out) -> int {
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, cap);
+    cudaError_t e = cudaMallocAsync(&p, cap, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return e == cudaErrorMemoryAllocation ? BT_ENOMEM : BT_ECUDA;
     }
-    out = std::shared_ptr<void>(p, [](void* x) { cudaFree(x); });
+    out = std::shared_ptr<void>(p, [](void* x) {
+      cudaFreeAsync(x, cudaStreamPerThread);
+      cudaStreamSynchronize(cudaStreamPerThread);
+    });
     return BT_OK;
   };
   std::shared_ptr<void> pool;
@@ -1591,9 +1601,10 @@ int run_batch(const M& m, const uint8_t* const* texts, const uint32_t* taus, con
     const uint64_t full = std::min<uint64_t>((uint64_t)(nd - r), (uint64_t)nsm * ctas_per_sm);
     uint32_t e = r;
     uint64_t grid;
-    if (full * top <= budget) {
+    const uint64_t cap = o.batch_ctas ? o.batch_ctas : ~0ull;
+    if (std::min<uint64_t>(full, cap) * top <= budget) {
       e = (uint32_t)nd;
-      grid = full;
+      grid = std::min<uint64_t>(full, cap);
     } else {
       // The class: the documents of the order whose need is within 4x of the
       // first one's, with a grid sized for the largest of them.
@@ -1603,7 +1614,7 @@ int run_batch(const M& m, const uint8_t* const* texts, const uint32_t* taus, con
         top = std::max<uint64_t>(top, out_align(order[e]->need));
         e++;
       }
-      grid = std::min<uint64_t>((uint64_t)(e - r), budget / top);
+      grid = std::min<uint64_t>({(uint64_t)(e - r), budget / top, cap});
       if (grid == 0) grid = 1;
     }
     cls.push_back(Cls{r, e - r, top, (unsigned)grid});
@@ -1652,7 +1663,8 @@ int run_batch(const M& m, const uint8_t* const* texts, const uint32_t* taus, con
       P2.pool = (char*)pool2.get();
       P2.pool_cap = cap2;
       const unsigned grid = (unsigned)std::max<uint64_t>(
-          1, std::min<uint64_t>({(uint64_t)hd2.size(), (uint64_t)nsm * ctas_per_sm, scratch_max / top}));
+          1, std::min<uint64_t>({(uint64_t)hd2.size(), (uint64_t)nsm * ctas_per_sm, scratch_max / top,
+                                 o.batch_ctas ? (uint64_t)o.batch_ctas : ~0ull}));
       BT_TRY(launch_docs(m, P2, order, 0, (uint32_t)hd2.size(), threads, ctas_per_sm, grid, top, d_scratch,
                          d_next, s));
       BT_CUDA(cudaMemcpyAsync(res.data(), d_res, nd * sizeof(BRes), cudaMemcpyDeviceToHost, s));

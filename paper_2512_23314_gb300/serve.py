@@ -1,18 +1,27 @@
 """Serving loop: continuous batching of block-tree builds under an HBM budget.
 
-Documents arrive over time.  A document is admitted when its estimated
-device footprint fits in the budget next to the builds in flight and the
-trees kept resident.  The oldest resident trees are evicted to make room.
-Admitted documents go to `nworkers` worker threads, each issuing its builds
-and queries on its own CUDA stream through the C ABI.  A document that
-arrives while others are on the GPU therefore starts as soon as a worker and
-memory are free, and its kernels overlap theirs.  After its build, every
-document answers a batch of mixed access / rank / select queries on its
-resident tree.
+Documents arrive over time.  `lanes` host threads serve them; each lane owns
+a CUDA stream and repeatedly takes work from the arrival queue:
 
-Latencies: build = arrival -> tree ready; query = one batch of queries
-(submission -> answers on the host).  Reported as p50 / p99 with sustained
-documents per second.
+* small documents (at most `small_max` bytes): every one waiting, in arrival
+  order, up to `max_batch_docs` and as far as the HBM budget admits them, as
+  one micro-batch built by bt_build_batch -- the persistent batched kernel,
+  on 1/lanes of the SMs, so the micro-batches of different lanes run side by
+  side on the device;
+* a large document: alone, with bt_build_ex on the lane's stream (the whole
+  GPU's level kernels for one text).
+
+A document that arrives while others are on the GPU is taken by the next
+lane that frees up, and its work overlaps theirs.  Admission charges an
+estimate of each document's device footprint against the budget; the oldest
+resident trees are evicted to make room.  After its build every document
+answers a batch of mixed access / rank / select queries on its resident tree
+(on the lane's stream).
+
+Reported: p50 / p99 build latency (arrival -> tree ready) and query-batch
+latency, admission wait (arrival -> build start), offered and sustained
+documents per second, the largest backlog of waiting documents, the number
+of micro-batches and their mean size.
 """
 from __future__ import annotations
 
@@ -43,6 +52,7 @@ class DocResult:
     built: float = 0.0
     queried: float = 0.0
     query_batch_s: float = 0.0
+    batched: bool = False
     export: bytes | None = None
     queries: dict | None = None     # kept (arguments, answers) per query kind
 
@@ -51,13 +61,20 @@ class DocResult:
 class Report:
     docs: int
     wall_s: float
+    offered_docs_per_s: float
     docs_per_s: float
     mb_per_s: float
     build_p50_ms: float
     build_p99_ms: float
+    admission_wait_p50_ms: float
+    admission_wait_p99_ms: float
     query_batch_p50_ms: float
     query_batch_p99_ms: float
     queries_per_doc: int
+    max_backlog: int
+    batches: int
+    mean_batch_docs: float
+    large_docs: int
     max_concurrent: int
     evictions: int
     results: list = field(default_factory=list, repr=False)
@@ -69,14 +86,18 @@ class Report:
 
 
 class Server:
-    def __init__(self, hbm_budget: int = 120 << 30, nworkers: int = 8, queries_per_doc: int = 10_000,
-                 keep_exports: bool = False, keep_queries: int = 0, seed: int = 0):
+    def __init__(self, hbm_budget: int = 120 << 30, lanes: int = 4, queries_per_doc: int = 10_000,
+                 small_max: int = 4 << 20, max_batch_docs: int = 512, keep_exports: bool = False,
+                 keep_queries: int = 0, seed: int = 0, sm_count: int | None = None):
         self.budget = hbm_budget
-        self.nworkers = nworkers
+        self.lanes = lanes
         self.qpd = queries_per_doc
+        self.small_max = small_max
+        self.max_batch_docs = max_batch_docs
         self.keep_exports = keep_exports
         self.keep_queries = keep_queries
         self.seed = seed
+        self.sm_count = sm_count
         self._lock = threading.Condition()
         self._charged = 0
         self._resident = collections.OrderedDict()  # index -> (tree handle, bytes)
@@ -85,21 +106,36 @@ class Server:
         self._evictions = 0
 
     # -- memory accounting ---------------------------------------------------
+    def _fits_locked(self, need: int) -> bool:
+        """Evict the oldest resident trees until `need` fits; True if it does."""
+        while self._charged + need > self.budget and self._resident:
+            _, (h, b) = self._resident.popitem(last=False)
+            bt.bt_free(h)
+            self._charged -= b
+            self._evictions += 1
+        return self._charged + need <= self.budget
+
+    def _charge_locked(self, need: int):
+        self._charged += need
+        self._inflight += 1
+        self._max_inflight = max(self._max_inflight, self._inflight)
+
     def _admit(self, need: int):
+        """Block until `need` bytes fit (a document larger than the budget
+        still runs, alone, once nothing else is in flight)."""
         with self._lock:
-            while self._charged + need > self.budget:
-                if self._resident:
-                    _, (h, b) = self._resident.popitem(last=False)
-                    bt.bt_free(h)
-                    self._charged -= b
-                    self._evictions += 1
-                    continue
+            while not self._fits_locked(need):
                 if self._inflight == 0:
-                    break  # a single document larger than the budget still runs alone
+                    break
                 self._lock.wait()
-            self._charged += need
-            self._inflight += 1
-            self._max_inflight = max(self._max_inflight, self._inflight)
+            self._charge_locked(need)
+
+    def _try_admit(self, need: int) -> bool:
+        with self._lock:
+            if not self._fits_locked(need):
+                return False
+            self._charge_locked(need)
+            return True
 
     def _release(self, estimate: int):
         """A document whose build or queries failed: its admission charge and
@@ -165,58 +201,110 @@ class Server:
         t_start = time.perf_counter()
         n_total = len(arrivals)
         finished = [0]
-
         errors = []
+        stats = {"backlog": 0, "batches": 0, "batch_docs": 0, "large": 0}
+        if self.sm_count is None:
+            try:
+                self.sm_count = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+            except Exception:  # no device: host tests with fake library calls
+                self.sm_count = 152
+        ctas = max(1, self.sm_count // max(1, self.lanes))
 
-        def finish_one():
+        def finish(k: int):
             with qlock:
-                finished[0] += 1
-                if finished[0] == n_total:
+                finished[0] += k
+                if finished[0] >= n_total:
                     done.set()
                 qlock.notify_all()
 
-        def serve_one(i, stream, rng, opts):
-            a = arrivals[i]
-            r = results[i]
-            est = estimate_bytes(r.n)
-            self._admit(est)
-            h = None
-            try:
-                r.start = time.perf_counter() - t_start
-                h = bt.bt_build_ex(a.doc.text, r.n, a.doc.sigma, a.doc.tau, a.doc.leaf_len, opts,
-                                   stream.cuda_stream)
-                r.built = time.perf_counter() - t_start
-                if self.keep_exports:
-                    r.export = bt.bt_export(h)
-                r.query_batch_s, r.queries = self._queries(h, r.n, rng, stream, self.keep_queries)
-                r.queried = time.perf_counter() - t_start
-            except BaseException:
-                if h is not None:
-                    bt.bt_free(h)
-                self._release(est)
-                raise
-            self._retire(i, h, est)
+        def take():
+            """The next unit of work: [one large document] or [small ones]."""
+            with qlock:
+                while not pending and not done.is_set():
+                    qlock.wait()
+                if not pending:
+                    return None
+                first = pending[0]
+                if results[first].n > self.small_max:
+                    pending.popleft()
+                    return [first]
+                batch = []
+                while pending and len(batch) < self.max_batch_docs and results[pending[0]].n <= self.small_max:
+                    batch.append(pending.popleft())
+                return batch
 
-        def worker(widx: int):
+        def serve_unit(unit, stream, rng):
+            ests = [estimate_bytes(results[i].n) for i in unit]
+            # The first document waits for room; the rest join the batch only
+            # while they fit now, and go back to the queue otherwise.
+            self._admit(ests[0])
+            admitted = 1
+            while admitted < len(unit) and self._try_admit(ests[admitted]):
+                admitted += 1
+            if admitted < len(unit):
+                with qlock:
+                    for i in reversed(unit[admitted:]):
+                        pending.appendleft(i)
+                    qlock.notify_all()
+                unit, ests = unit[:admitted], ests[:admitted]
+            handles = [None] * len(unit)
+            try:
+                t0 = time.perf_counter() - t_start
+                for i in unit:
+                    results[i].start = t0
+                docs = [arrivals[i].doc for i in unit]
+                if len(unit) == 1 and results[unit[0]].n > self.small_max:
+                    d = docs[0]
+                    handles[0] = bt.bt_build_ex(d.text, len(d.text), d.sigma, d.tau, d.leaf_len,
+                                                bt.bt_opts_default(), stream.cuda_stream)
+                    with qlock:
+                        stats["large"] += 1
+                else:
+                    o, keep = bt.BuildOptions(batch_ctas=ctas).to_c()
+                    handles = bt.bt_build_batch([d.text for d in docs], [len(d.text) for d in docs],
+                                                [d.sigma for d in docs], [d.tau for d in docs],
+                                                [d.leaf_len for d in docs], o)
+                    del keep
+                    for i in unit:
+                        results[i].batched = True
+                    with qlock:
+                        stats["batches"] += 1
+                        stats["batch_docs"] += len(unit)
+                t1 = time.perf_counter() - t_start
+                for i, h in zip(unit, handles):
+                    r = results[i]
+                    r.built = t1
+                    if self.keep_exports:
+                        r.export = bt.bt_export(h)
+                    r.query_batch_s, r.queries = self._queries(h, r.n, rng, stream, self.keep_queries)
+                    r.queried = time.perf_counter() - t_start
+            except BaseException:
+                for h in handles:
+                    if h is not None:
+                        bt.bt_free(h)
+                for e in ests:
+                    self._release(e)
+                raise
+            for i, h, e in zip(unit, handles, ests):
+                self._retire(i, h, e)
+            return len(unit)
+
+        def lane(widx: int):
             stream = torch.cuda.Stream()
             rng = np.random.default_rng(self.seed * 1000 + widx)
-            opts = bt.bt_opts_default()
             while True:
-                with qlock:
-                    while not pending and not done.is_set():
-                        qlock.wait()
-                    if not pending:
-                        return
-                    i = pending.popleft()
+                unit = take()
+                if unit is None:
+                    return
                 try:
-                    serve_one(i, stream, rng, opts)
+                    k = serve_unit(unit, stream, rng)
                 except BaseException as e:  # recorded; run() re-raises the first one
                     with qlock:
                         errors.append(e)
-                finally:
-                    finish_one()
+                    k = len(unit)
+                finish(k)
 
-        threads = [threading.Thread(target=worker, args=(w,), daemon=True) for w in range(self.nworkers)]
+        threads = [threading.Thread(target=lane, args=(w,), daemon=True) for w in range(self.lanes)]
         for th in threads:
             th.start()
         for i, a in enumerate(arrivals):
@@ -225,12 +313,14 @@ class Server:
                 time.sleep(delay)
             with qlock:
                 pending.append(i)
+                stats["backlog"] = max(stats["backlog"], len(pending))
                 qlock.notify()
         if n_total == 0:
             done.set()
         with qlock:
-            while not done.is_set():
+            while not done.is_set() and not (errors and not any(th.is_alive() for th in threads)):
                 qlock.wait(timeout=1.0)
+            done.set()
             qlock.notify_all()
         for th in threads:
             th.join()
@@ -239,17 +329,21 @@ class Server:
         if errors:
             raise errors[0]
         build_lat = np.array([r.built - r.arrival for r in results]) * 1e3
+        wait = np.array([r.start - r.arrival for r in results]) * 1e3
         q_lat = np.array([r.query_batch_s for r in results]) * 1e3
         total_bytes = sum(r.n for r in results)
-        rep = Report(
-            docs=n_total, wall_s=wall, docs_per_s=n_total / wall, mb_per_s=total_bytes / wall / 1e6,
-            build_p50_ms=float(np.percentile(build_lat, 50)) if n_total else 0.0,
-            build_p99_ms=float(np.percentile(build_lat, 99)) if n_total else 0.0,
-            query_batch_p50_ms=float(np.percentile(q_lat, 50)) if n_total else 0.0,
-            query_batch_p99_ms=float(np.percentile(q_lat, 99)) if n_total else 0.0,
-            queries_per_doc=3 * (self.qpd // 3), max_concurrent=self._max_inflight,
-            evictions=self._evictions, results=results)
-        return rep
+        span = arrivals[-1].t if n_total else 0.0
+        pct = (lambda a, p: float(np.percentile(a, p)) if n_total else 0.0)
+        return Report(
+            docs=n_total, wall_s=wall, offered_docs_per_s=n_total / span if span > 0 else 0.0,
+            docs_per_s=n_total / wall if wall > 0 else 0.0, mb_per_s=total_bytes / wall / 1e6 if wall > 0 else 0.0,
+            build_p50_ms=pct(build_lat, 50), build_p99_ms=pct(build_lat, 99),
+            admission_wait_p50_ms=pct(wait, 50), admission_wait_p99_ms=pct(wait, 99),
+            query_batch_p50_ms=pct(q_lat, 50), query_batch_p99_ms=pct(q_lat, 99),
+            queries_per_doc=3 * (self.qpd // 3), max_backlog=stats["backlog"], batches=stats["batches"],
+            mean_batch_docs=stats["batch_docs"] / stats["batches"] if stats["batches"] else 0.0,
+            large_docs=stats["large"], max_concurrent=self._max_inflight, evictions=self._evictions,
+            results=results)
 
     def close(self):
         with self._lock:

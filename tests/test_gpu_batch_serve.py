@@ -64,12 +64,15 @@ def test_served_results_equal_standalone():
     arrivals = workloads.serve_arrivals(rate=2000.0, duration=0.03, min_len=1 << 10,
                                         max_len=256 << 10, seed=5)
     assert len(arrivals) > 20
-    srv = serve.Server(hbm_budget=256 << 20, nworkers=6, queries_per_doc=300, keep_exports=True,
-                       keep_queries=40)
+    # Documents above 128 KiB are built alone (bt_build_ex), the others in
+    # micro-batches of the batched kernel: both paths serve in the mix.
+    srv = serve.Server(hbm_budget=256 << 20, lanes=4, queries_per_doc=300, small_max=128 << 10,
+                       keep_exports=True, keep_queries=40)
     rep = srv.run(arrivals)
     srv.close()
     assert rep.docs == len(arrivals)
     assert rep.max_concurrent >= 2          # work really overlapped
+    assert rep.batches >= 1 and rep.large_docs >= 1
     for i, (a, r) in enumerate(zip(arrivals, rep.results)):
         assert r.export == alone(a.doc)
         assert r.built >= r.arrival and r.queried >= r.built

@@ -19,7 +19,7 @@ def fake_lib(monkeypatch):
 
 
 def test_admission_evicts_oldest_and_charges_real_bytes(fake_lib):
-    s = serve.Server(hbm_budget=100, nworkers=1)
+    s = serve.Server(hbm_budget=100, lanes=1)
     s._admit(40)
     s._retire(0, "h0", 40)  # the estimate 40 becomes the real 10
     s._admit(40)
@@ -33,7 +33,7 @@ def test_admission_evicts_oldest_and_charges_real_bytes(fake_lib):
 
 
 def test_document_larger_than_budget_runs_alone(fake_lib):
-    s = serve.Server(hbm_budget=100, nworkers=1)
+    s = serve.Server(hbm_budget=100, lanes=1)
     s._admit(40)
     s._retire(0, "h0", 40)
     s._admit(500)  # evicts everything resident, then runs alone over the budget
@@ -41,7 +41,7 @@ def test_document_larger_than_budget_runs_alone(fake_lib):
 
 
 def test_admission_waits_for_builds_in_flight(fake_lib):
-    s = serve.Server(hbm_budget=100, nworkers=2)
+    s = serve.Server(hbm_budget=100, lanes=2)
     s._admit(80)  # in flight, nothing resident to evict
     done = threading.Event()
 
@@ -84,7 +84,8 @@ def test_worker_error_is_raised_and_releases_its_charge(fake_lib, monkeypatch):
 
     monkeypatch.setattr(serve.bt, "bt_build_ex", fake_build)
     monkeypatch.setattr(serve.Server, "_queries", lambda self, h, n, rng, stream, keep=0: (0.0, None))
-    s = serve.Server(hbm_budget=1 << 40, nworkers=3)
+    # small_max=0: every document is built alone with bt_build_ex.
+    s = serve.Server(hbm_budget=1 << 40, lanes=3, small_max=0)
     t0 = time.perf_counter()
     with pytest.raises(serve.bt.BTError):
         s.run(_arrivals(6))
@@ -104,7 +105,37 @@ def test_every_worker_failing_still_returns(fake_lib, monkeypatch):
         raise RuntimeError("device lost")
 
     monkeypatch.setattr(serve.bt, "bt_build_ex", fail)
-    s = serve.Server(hbm_budget=1 << 40, nworkers=2)
+    s = serve.Server(hbm_budget=1 << 40, lanes=2, small_max=0)
     with pytest.raises(RuntimeError, match="device lost"):
         s.run(_arrivals(5))
     assert s._inflight == 0 and s._charged == 0
+
+
+def test_small_documents_go_out_in_micro_batches(fake_lib, monkeypatch):
+    """Small documents waiting together are built by one bt_build_batch call
+    on 1/lanes of the SMs; a failing micro-batch releases every charge."""
+    monkeypatch.setattr(serve.torch.cuda, "Stream", _FakeStream)
+    monkeypatch.setattr(serve.torch.cuda, "synchronize", lambda *a: None)
+    calls = []
+
+    def fake_batch(texts, ns, sigmas, taus, leafs, opts, nworkers=0):
+        calls.append((list(ns), opts.batch_ctas))
+        return [f"b{n}" for n in ns]
+
+    monkeypatch.setattr(serve.bt, "bt_build_batch", fake_batch)
+    monkeypatch.setattr(serve.Server, "_queries", lambda self, h, n, rng, stream, keep=0: (0.0, None))
+    s = serve.Server(hbm_budget=1 << 40, lanes=2, small_max=1 << 20, sm_count=152)
+    rep = s.run(_arrivals(40))  # all arrive at t = 0
+    assert rep.docs == 40 and rep.batches == len(calls) >= 1
+    assert sorted(n for ns, _ in calls for n in ns) == list(range(64, 104))
+    assert all(ctas == 76 for _, ctas in calls)
+    assert rep.mean_batch_docs > 1 and s._inflight == 0 and len(s._resident) == 40
+
+    def failing(*a, **k):
+        raise RuntimeError("batch failed")
+
+    monkeypatch.setattr(serve.bt, "bt_build_batch", failing)
+    s2 = serve.Server(hbm_budget=1 << 40, lanes=2, sm_count=152)
+    with pytest.raises(RuntimeError, match="batch failed"):
+        s2.run(_arrivals(10))
+    assert s2._inflight == 0 and s2._charged == 0
