@@ -145,11 +145,15 @@ int bt_build_batch(const uint8_t* const* texts, const uint64_t* ns, const uint32
                    const bt_opts* opts, uint32_t nworkers, bt_tree** outs);
 
 /* Measurement hooks of the batched build (not part of the paper's method).
- * bt_batch_report: what the last bt_build_batch call of the process did, 9
+ * bt_batch_report: what the last bt_build_batch call of the process did, 11
  * u64: documents built by the batched kernel, documents built by host
  * workers, kernel launches, documents built a second time because the output
  * pool ran out, threads per CTA, CTAs per SM, output pool bytes, CTA scratch
- * bytes, the largest grid.  bt_batch_cycles: for a tree from the batched
+ * bytes, the largest grid, the scan's window chunk (positions per lane and
+ * step), and the autotuner's trial builds in this call.  The launch shape
+ * (threads, CTAs per SM, chunk) of a batch of 1024 or more documents is
+ * chosen by timing each candidate on a seeded sample of the batch the first
+ * time a batch of its size class is built, and cached for the process.  bt_batch_cycles: for a tree from the batched
  * kernel, the SM clock cycles its CTA spent per phase (6 u64: set-up,
  * tables, window scan, verification/marks/pointers/split, pruning, output
  * and counters); zeros for other trees.  BT_EINVAL for null pointers or cap
@@ -274,6 +278,18 @@ typedef struct {
 void bt_profile_enable(int on);
 void bt_profile_reset(void);
 int bt_profile_read(bt_profile_entry* out, uint32_t cap, uint32_t* count);
+
+/* Test hooks for allocation failures (not part of the paper's method).
+ * bt_test_alloc_limit(bytes): from now on, any single device allocation a
+ * build makes (text copy, prefix fingerprints, level scratch, the batched
+ * build's buffers and output pool) that is larger than `bytes` fails as if
+ * the device were out of memory, so the build returns BT_ENOMEM; 0 removes
+ * the limit.  Process-wide; not for concurrent use with real builds.
+ * bt_device_pool_used: bytes currently allocated from the current device's
+ * stream-ordered memory pool (the library's builds allocate there), for
+ * checking that a failed build gave everything back. */
+void bt_test_alloc_limit(uint64_t bytes);
+int bt_device_pool_used(uint64_t* out);
 
 /* Number of kernels this library has launched in the process so far. */
 uint64_t bt_launch_count(void);

@@ -89,6 +89,9 @@ def lib() -> ctypes.CDLL:
     L.bt_launch_count.restype = u64
     L.bt_mulmod_bench.argtypes = [u32, u32, u64, vp, vp, P(u64)]
     L.bt_batch_report.argtypes = [vp, u32]
+    L.bt_test_alloc_limit.argtypes = [u64]
+    L.bt_test_alloc_limit.restype = None
+    L.bt_device_pool_used.argtypes = [P(u64)]
     L.bt_batch_cycles.argtypes = [vp, vp, u32]
     for name in ("bt_profile_read", "bt_build", "bt_build_ex", "bt_build_batch", "bt_access", "bt_rank", "bt_select",
                  "bt_query_batch", "bt_export", "bt_stats", "bt_prefix_fingerprints",
@@ -181,10 +184,10 @@ def bt_build_batch(texts, ns, sigmas, taus, leaf_lens, opts: bt_opts | None = No
 
 def bt_batch_report() -> dict:
     """What the last bt_build_batch call did (measurement hook)."""
-    a = (ctypes.c_uint64 * 9)()
-    _check(lib().bt_batch_report(a, 9), "bt_batch_report")
+    a = (ctypes.c_uint64 * 11)()
+    _check(lib().bt_batch_report(a, 11), "bt_batch_report")
     names = ("kernel_docs", "worker_docs", "launches", "retried", "threads", "ctas_per_sm", "pool_bytes",
-             "scratch_bytes", "max_grid")
+             "scratch_bytes", "max_grid", "chunk", "tuning_trials")
     return dict(zip(names, list(a)))
 
 
@@ -193,6 +196,18 @@ def bt_batch_cycles(t: int) -> list[int]:
     a = (ctypes.c_uint64 * 6)()
     _check(lib().bt_batch_cycles(t, a, 6), "bt_batch_cycles")
     return list(a)
+
+
+def bt_test_alloc_limit(nbytes: int) -> None:
+    """Test hook: device allocations of a build larger than nbytes fail (0: off)."""
+    lib().bt_test_alloc_limit(nbytes)
+
+
+def bt_device_pool_used() -> int:
+    """Bytes allocated from the device's stream-ordered pool right now."""
+    v = ctypes.c_uint64()
+    _check(lib().bt_device_pool_used(ctypes.byref(v)), "bt_device_pool_used")
+    return v.value
 
 
 def bt_access(t: int, i: int) -> int:

@@ -24,8 +24,11 @@ int upload_view(bt_tree* t, cudaStream_t s);
 int batch_kernel_build(const uint8_t* const* texts, const uint64_t* ns, const uint32_t* sigmas,
                        const uint32_t* taus, const uint32_t* leaf_lens, uint64_t ndocs, const bt_opts& o,
                        std::vector<char>& routed, bt_tree** outs, uint32_t threads, uint32_t ctas_per_sm,
-                       cudaStream_t s);
-void batch_config(const uint64_t* ns, uint64_t ndocs, uint32_t* threads, uint32_t* ctas_per_sm);
+                       uint32_t chunk, cudaStream_t s);
+int batch_shape(const uint8_t* const* texts, const uint64_t* ns, const uint32_t* sigmas, const uint32_t* taus,
+                const uint32_t* leaf_lens, uint64_t ndocs, const bt_opts& o, cudaStream_t s, uint32_t* threads,
+                uint32_t* ctas_per_sm, uint32_t* chunk, uint64_t* tuned_now);
+void batch_report_tuned(uint64_t trials);
 void batch_report_workers(uint64_t docs);
 void batch_report_reset();
 int run_queries(const bt_tree* t, int kind, const uint64_t* d_args, uint64_t m, uint64_t* d_out,
@@ -38,6 +41,12 @@ void note_cuda_error(cudaError_t e, const char* what, const char* file, int line
 
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static std::atomic<uint64_t> g_alloc_limit{0};
+bool alloc_allowed(uint64_t bytes) {
+  const uint64_t lim = g_alloc_limit.load(std::memory_order_relaxed);
+  return lim == 0 || bytes <= lim;
+}
 
 namespace {
 struct ProfRec {
@@ -405,9 +414,15 @@ int bt_build_batch(const uint8_t* const* texts, const uint64_t* ns, const uint32
     int device = 0;
     if (cudaGetDevice(&device) == cudaSuccess) keep_pool_memory(device);
     cudaGetLastError();
-    uint32_t threads = 0, ctas = 0;
-    batch_config(ns, ndocs, &threads, &ctas);
-    rc = batch_kernel_build(texts, ns, sigmas, taus, leaf_lens, ndocs, o, routed, outs, threads, ctas, s);
+    uint32_t threads = 0, ctas = 0, chunk = 0;
+    uint64_t trials = 0;
+    rc = batch_shape(texts, ns, sigmas, taus, leaf_lens, ndocs, o, s, &threads, &ctas, &chunk, &trials);
+    if (rc == BT_OK) {
+      batch_report_reset();
+      rc = batch_kernel_build(texts, ns, sigmas, taus, leaf_lens, ndocs, o, routed, outs, threads, ctas, chunk,
+                              s);
+      batch_report_tuned(trials);
+    }
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
   }
@@ -594,6 +609,20 @@ int bt_profile_read(bt_profile_entry* out, uint32_t cap, uint32_t* count) {
 }
 
 uint64_t bt_launch_count(void) { return g_launches.load(); }
+
+void bt_test_alloc_limit(uint64_t bytes) { g_alloc_limit.store(bytes); }
+
+int bt_device_pool_used(uint64_t* out) {
+  if (!out) return BT_EINVAL;
+  int dev = 0;
+  BT_CUDA(cudaGetDevice(&dev));
+  cudaMemPool_t pool;
+  BT_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t used = 0;
+  BT_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+  *out = used;
+  return BT_OK;
+}
 
 const char* bt_strerror(int status) {
   switch (status) {

@@ -40,6 +40,8 @@
 #include <thread>
 #include <vector>
 
+#include <chrono>
+
 #include "bt_batch.cuh"
 
 namespace bt {
@@ -604,7 +606,8 @@ __device__ void level_pass(const M& m, const BParams& P, const BDoc& D, Cta& C, 
     const ScanArgs A{H, W.bt, W.pt, bmask, pmask, b, r, Bb, Br, fp_tail, pretail, &C.lo_tailpair};
     if (b % 32 == 0) {
       constexpr int U = 4;
-      const uint32_t Ue = b / 32 < U ? (uint32_t)(b / 32) : U;  // positions per lane
+      const uint32_t Umax = P.scan_u && P.scan_u < (uint32_t)U ? P.scan_u : (uint32_t)U;
+      const uint32_t Ue = b / 32 < Umax ? (uint32_t)(b / 32) : Umax;  // positions per lane
       const uint32_t CH = 32 * Ue;
       const uint64_t cpb = (b + CH - 1) / CH;
       const unsigned lane = tid & 31, nw = nt >> 5;
@@ -1265,6 +1268,7 @@ __device__ void write_output(const BParams& P, const BDoc& D, Cta& C, char* scr,
       lv.c = C.c[l];
       lv.b = bsz[l];
       lv.arity = C.arity[l];
+      lv.bshift = block_shift(bsz[l]);
       lv.st = (const uint64_t*)(out + s_ol[l].st);
       lv.mw = (const uint32_t*)(out + s_ol[l].mw);
       lv.mr = (const uint32_t*)(out + s_ol[l].mr);
@@ -1374,7 +1378,7 @@ __global__ void __launch_bounds__(NT, MINB) k_batch(BParams P, M m) {
 // What the last batched build did (bt_batch_report).
 struct Report {
   uint64_t kernel_docs, worker_docs, launches, retried, threads, ctas_per_sm, pool_bytes, scratch_bytes,
-      max_grid;
+      max_grid, chunk, tuned;
 };
 std::mutex g_report_mu;
 Report g_report{};
@@ -1458,6 +1462,7 @@ struct DevFree {
   template <class T>
   int alloc(T** out, uint64_t count) {
     void* q = nullptr;
+    if (!alloc_allowed((count ? count : 1) * sizeof(T))) return BT_ENOMEM;
     cudaError_t e = cudaMallocAsync(&q, (count ? count : 1) * sizeof(T), s);
     if (e != cudaSuccess) {
       note_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
@@ -1473,7 +1478,7 @@ struct DevFree {
 template <class M>
 int run_batch(const M& m, const uint8_t* const* texts, const uint32_t* taus, const uint32_t* leaf_lens,
               const bt_opts& o, std::vector<DocPlan>& plans, const std::vector<uint64_t>& sizes,
-              unsigned threads, unsigned ctas_per_sm, bt_tree** outs, cudaStream_t s) {
+              unsigned threads, unsigned ctas_per_sm, unsigned chunk, bt_tree** outs, cudaStream_t s) {
   const uint64_t nd = plans.size();
   if (nd == 0) return BT_OK;
   int device = 0;
@@ -1548,6 +1553,7 @@ int run_batch(const M& m, const uint8_t* const* texts, const uint32_t* taus, con
   // is never freed while queries on it run).
   auto make_pool = [&](uint64_t cap, std::shared_ptr<void>& out) -> int {
     void* p = nullptr;
+    if (!alloc_allowed(cap)) return BT_ENOMEM;
     cudaError_t e = cudaMallocAsync(&p, cap, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -1577,6 +1583,7 @@ int run_batch(const M& m, const uint8_t* const* texts, const uint32_t* taus, con
   P.pw32 = d_pw;
   P.prune = o.prune ? 1 : 0;
   P.max_rounds = o.max_rounds ? o.max_rounds : 4096;
+  P.scan_u = chunk;
 
   // Size classes: consecutive documents (in decreasing scratch need) whose
   // need is within 4x of the class's first; one launch per class, with as
@@ -1744,6 +1751,7 @@ int run_batch(const M& m, const uint8_t* const* texts, const uint32_t* taus, con
     g_report.retried = retried;
     g_report.threads = threads;
     g_report.ctas_per_sm = ctas_per_sm;
+    g_report.chunk = chunk;
     g_report.pool_bytes = pool_cap;
     g_report.scratch_bytes = scratch_max;
     g_report.max_grid = 0;
@@ -1762,7 +1770,7 @@ int run_batch(const M& m, const uint8_t* const* texts, const uint32_t* taus, con
 int batch_kernel_build(const uint8_t* const* texts, const uint64_t* ns, const uint32_t* sigmas,
                        const uint32_t* taus, const uint32_t* leaf_lens, uint64_t ndocs, const bt_opts& o,
                        std::vector<char>& routed, bt_tree** outs, uint32_t threads, uint32_t ctas_per_sm,
-                       cudaStream_t s) {
+                       uint32_t chunk, cudaStream_t s) {
   if (threads < 64 || threads > kMaxBThreads || threads % 32) return BT_EINVAL;
   if (ctas_per_sm == 0) ctas_per_sm = 1;
   if (o.modulus && (o.modulus < 300 || o.modulus >= (1ull << 32))) return BT_EINVAL;
@@ -1789,8 +1797,10 @@ int batch_kernel_build(const uint8_t* const* texts, const uint64_t* ns, const ui
     plans.push_back(pl);
     routed[d] = 1;
   }
-  if (o.modulus) return run_batch(SmallMod{o.modulus}, texts, taus, leaf_lens, o, plans, sizes, threads, ctas_per_sm, outs, s);
-  return run_batch(Mersenne61{}, texts, taus, leaf_lens, o, plans, sizes, threads, ctas_per_sm, outs, s);
+  if (o.modulus)
+    return run_batch(SmallMod{o.modulus}, texts, taus, leaf_lens, o, plans, sizes, threads, ctas_per_sm, chunk,
+                     outs, s);
+  return run_batch(Mersenne61{}, texts, taus, leaf_lens, o, plans, sizes, threads, ctas_per_sm, chunk, outs, s);
 }
 
 void batch_report_workers(uint64_t docs) {
@@ -1803,25 +1813,128 @@ void batch_report_reset() {
   g_report = Report{};
 }
 
-// Launch shape of the batched kernel: threads per CTA and CTAs per SM.
-void batch_config(const uint64_t* ns, uint64_t ndocs, uint32_t* threads, uint32_t* ctas_per_sm) {
-  (void)ns;
-  (void)ndocs;
-  *threads = 1024;
-  *ctas_per_sm = 1;
-  if (const char* e = getenv("BT_BATCH_THREADS")) *threads = (uint32_t)atoi(e);
-  if (const char* e = getenv("BT_BATCH_CTAS")) *ctas_per_sm = (uint32_t)atoi(e);
+// ---------------------------------------------------------------------------
+// Autotuner of the batched kernel's launch shape: threads per CTA, CTAs per
+// SM and the window chunk of the scan (positions per lane and step).  For a
+// batch of at least kTuneMinDocs documents whose size class has no cached
+// choice, each candidate builds the same seeded sample of the batch: every
+// k-th document no longer than the batch's 75th length percentile, about
+// 1/16 of the batch but at least two documents per CTA of a full grid, so
+// that every SM stays busy during the trial.  A candidate's cost is the SM
+// time it spent: the sum over the sample of the cycles of each document's
+// CTA, divided by the CTAs that share an SM (a wall-clock time would measure
+// the sample's longest document instead).  The cheapest is cached per (log2
+// of the mean length, log2 of the longest, log2 of the batch size) for the
+// rest of the process.  Smaller batches use the default shape.
+namespace {
+struct Shape {
+  uint32_t threads, ctas, chunk;
+};
+constexpr Shape kShapes[] = {{1024, 1, 4}, {1024, 1, 2}, {512, 1, 4}, {512, 2, 4}};
+constexpr uint64_t kTuneMinDocs = 1024;
+std::mutex g_tune_mu;
+std::vector<std::pair<uint64_t, Shape>> g_tuned;
+
+uint64_t tune_key(const uint64_t* ns, uint64_t ndocs) {
+  uint64_t sum = 0, mx = 0;
+  for (uint64_t d = 0; d < ndocs; d++) {
+    sum += ns[d];
+    mx = std::max<uint64_t>(mx, ns[d]);
+  }
+  auto lg = [](uint64_t x) {
+    uint64_t l = 0;
+    while (x > 1) {
+      x >>= 1;
+      l++;
+    }
+    return l;
+  };
+  return (lg(sum / std::max<uint64_t>(ndocs, 1)) << 16) | (lg(mx) << 8) | lg(ndocs);
+}
+}  // namespace
+
+int batch_shape(const uint8_t* const* texts, const uint64_t* ns, const uint32_t* sigmas, const uint32_t* taus,
+                const uint32_t* leaf_lens, uint64_t ndocs, const bt_opts& o, cudaStream_t s, uint32_t* threads,
+                uint32_t* ctas_per_sm, uint32_t* chunk, uint64_t* tuned_now) {
+  Shape best = kShapes[0];
+  *tuned_now = 0;
+  if (const char* e = getenv("BT_BATCH_SHAPE")) {  // "threads,ctas,chunk": a fixed shape for measurements
+    unsigned a = 0, b2 = 0, c = 0;
+    if (sscanf(e, "%u,%u,%u", &a, &b2, &c) == 3 && a && b2 && c) best = Shape{a, b2, c};
+  } else if (ndocs >= kTuneMinDocs && !o.batch_ctas) {
+    const uint64_t key = tune_key(ns, ndocs);
+    bool found = false;
+    {
+      std::lock_guard<std::mutex> g(g_tune_mu);
+      for (auto& kv : g_tuned)
+        if (kv.first == key) {
+          best = kv.second;
+          found = true;
+        }
+    }
+    if (!found) {
+      // The sample: every k-th document, about 1/16 of the batch but at least
+      // two per CTA of a full grid.
+      std::vector<uint64_t> lens(ns, ns + ndocs);
+      std::nth_element(lens.begin(), lens.begin() + ndocs * 3 / 4, lens.end());
+      const uint64_t cap75 = lens[ndocs * 3 / 4];
+      const uint64_t want = std::max<uint64_t>(ndocs / 16, 2ull * device_sm_count() * 2);
+      const uint64_t step = std::max<uint64_t>(1, ndocs * 3 / 4 / want);
+      std::vector<const uint8_t*> st;
+      std::vector<uint64_t> sn;
+      std::vector<uint32_t> ss, stau, sl;
+      for (uint64_t d = 0; d < ndocs; d += step) {
+        if (ns[d] > cap75) continue;
+        st.push_back(texts[d]);
+        sn.push_back(ns[d]);
+        ss.push_back(sigmas[d]);
+        stau.push_back(taus[d]);
+        sl.push_back(leaf_lens[d]);
+      }
+      double best_cost = 1e300;
+      for (const Shape& sh : kShapes) {
+        std::vector<char> routed;
+        std::vector<bt_tree*> outs(st.size(), nullptr);
+        const int rc = batch_kernel_build(st.data(), sn.data(), ss.data(), stau.data(), sl.data(), st.size(), o,
+                                          routed, outs.data(), sh.threads, sh.ctas, sh.chunk, s);
+        cudaStreamSynchronize(s);
+        double cycles = 0;
+        for (bt_tree* t : outs)
+          if (t)
+            for (int i = 0; i < 6; i++) cycles += (double)t->batch_cycles[i];
+        for (bt_tree* t : outs) bt_free(t);
+        if (rc != BT_OK) return rc;
+        const double cost = cycles / sh.ctas;
+        if (cost < best_cost) {
+          best_cost = cost;
+          best = sh;
+        }
+        (*tuned_now)++;
+      }
+      std::lock_guard<std::mutex> g(g_tune_mu);
+      g_tuned.emplace_back(key, best);
+    }
+  }
+  *threads = best.threads;
+  *ctas_per_sm = best.ctas;
+  *chunk = best.chunk;
+  return BT_OK;
+}
+
+void batch_report_tuned(uint64_t trials) {
+  std::lock_guard<std::mutex> g(g_report_mu);
+  g_report.tuned = trials;
 }
 
 }  // namespace bt
 
 extern "C" int bt_batch_report(uint64_t* out, uint32_t cap) {
   using namespace bt;
-  if (!out || cap < 9) return BT_EINVAL;
+  if (!out || cap < 11) return BT_EINVAL;
   std::lock_guard<std::mutex> g(g_report_mu);
-  const uint64_t v[9] = {g_report.kernel_docs, g_report.worker_docs, g_report.launches, g_report.retried,
-                         g_report.threads, g_report.ctas_per_sm, g_report.pool_bytes, g_report.scratch_bytes,
-                         g_report.max_grid};
+  const uint64_t v[11] = {g_report.kernel_docs, g_report.worker_docs, g_report.launches, g_report.retried,
+                          g_report.threads, g_report.ctas_per_sm, g_report.pool_bytes, g_report.scratch_bytes,
+                          g_report.max_grid, g_report.chunk, g_report.tuned};
   memcpy(out, v, sizeof(v));
   return BT_OK;
 }

@@ -130,6 +130,7 @@ struct Level {
 struct LevelView {
   uint64_t c, b;
   uint32_t arity;
+  uint32_t bshift;  // log2(b) when b is a power of two, else 0xFF
   const uint64_t* st;
   const uint32_t* mw;
   const uint32_t* mr;
@@ -139,6 +140,13 @@ struct LevelView {
   const void* pc;
   uint32_t cw;
 };
+
+__host__ __device__ inline uint32_t block_shift(uint64_t b) {
+  if (b == 0 || (b & (b - 1))) return 0xFFu;
+  uint32_t s = 0;
+  while ((1ull << s) < b) s++;
+  return s;
+}
 
 // Bytes per symbol counter of a level with block length b: a count never
 // exceeds b.
@@ -247,6 +255,11 @@ struct Status {
   unsigned long long pad[4];
 };
 
+// Test hook (bt_test_alloc_limit): the largest single device allocation a
+// build may make; larger ones fail as if the device were out of memory.
+// 0: no limit.
+bool alloc_allowed(uint64_t bytes);
+
 // Scratch allocator bound to a stream (stream-ordered pool allocations).
 struct Scratch {
   cudaStream_t s;
@@ -255,6 +268,7 @@ struct Scratch {
   template <class T>
   int alloc(T** p, uint64_t count) {
     void* q = nullptr;
+    if (!alloc_allowed((count ? count : 1) * sizeof(T))) return BT_ENOMEM;
     cudaError_t e = cudaMallocAsync(&q, (count ? count : 1) * sizeof(T), s);
     if (e != cudaSuccess) {
       note_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
@@ -291,6 +305,7 @@ struct Arena {
     base = nullptr;
     cap = 0;
     const uint64_t want = need + need / 4;
+    if (!alloc_allowed(want)) return BT_ENOMEM;
     cudaError_t e = cudaMallocAsync((void**)&base, want, s);
     if (e != cudaSuccess) {
       note_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);

@@ -12,6 +12,8 @@
 // it adds the counts of the children left of the one holding i; at an
 // unmarked block it continues in its target (ptr or ptr+1) and subtracts
 // pc.  select mirrors it.  One thread answers one query.
+#include <cstdlib>
+
 #include "bt_internal.cuh"
 
 namespace bt {
@@ -213,15 +215,51 @@ __device__ __forceinline__ uint64_t qlen(const TreeView& t, const LevelView& v, 
   return t.n - s < v.b ? t.n - s : v.b;
 }
 
+// Occurrences of byte c in p[0, o): four bytes per step from aligned words
+// (a per-byte compare, __vcmpeq4, then a population count).
+__device__ __forceinline__ uint64_t leaf_count(const uint8_t* p, uint64_t o, uint32_t c) {
+  uint64_t x = 0, acc = 0;
+  if ((((uintptr_t)p) & 3) == 0) {
+    const uint32_t cc = c * 0x01010101u;
+    const uint32_t* w = (const uint32_t*)p;
+    for (; x + 4 <= o; x += 4) acc += __popc(__vcmpeq4(w[x >> 2], cc)) >> 3;
+  }
+  for (; x < o; x++) acc += p[x] == c;
+  return acc;
+}
+
+// Position of the j-th occurrence (j >= 1) of byte c in p[0, len), or kNone.
+__device__ __forceinline__ uint64_t leaf_find(const uint8_t* p, uint64_t len, uint32_t c, uint64_t j) {
+  uint64_t x = 0;
+  if ((((uintptr_t)p) & 3) == 0) {
+    const uint32_t cc = c * 0x01010101u;
+    const uint32_t* w = (const uint32_t*)p;
+    for (; x + 4 <= len; x += 4) {
+      const uint32_t eq = __vcmpeq4(w[x >> 2], cc);
+      const uint32_t k = __popc(eq) >> 3;
+      if (k >= j) break;  // the j-th is in this word: bytes below
+      j -= k;
+    }
+  }
+  for (; x < len; x++)
+    if (p[x] == c && --j == 0) return x;
+  return kNone;
+}
+
+// x / b for the block length of a level (a shift when b is a power of two).
+__device__ __forceinline__ uint64_t div_b(uint64_t x, const LevelView& v) {
+  return v.bshift != 0xFFu ? x >> v.bshift : x / v.b;
+}
+
 __device__ uint64_t q_access(const TreeView& t, uint64_t i) {
   if (i >= t.n) return kNone;
   uint32_t l = 0;
-  uint64_t k = i / t.lv[0].b, x = i;
+  uint64_t k = div_b(i, t.lv[0]), x = i;
   for (uint32_t step = 0; step < 4 * t.L + 4; step++) {
     const LevelView& v = t.lv[l];
     if (qmarked(v, k)) {
       if (l + 1 == t.L) return t.leaf[qrank(v, k) * v.b + (x - v.st[k])];
-      k = qrank(v, k) * v.arity + (x - v.st[k]) / t.lv[l + 1].b;
+      k = qrank(v, k) * v.arity + div_b(x - v.st[k], t.lv[l + 1]);
       l++;
     } else {
       uint64_t P = v.ptr[k];
@@ -239,7 +277,7 @@ __device__ uint64_t q_rank(const TreeView& t, uint32_t c, uint64_t i) {
   const uint32_t S = t.S;
   const LevelView& r = t.lv[0];
   if (i == t.n) return t.pre[r.c * S + s];
-  uint64_t k = i / r.b, o = i - r.st[k];
+  uint64_t k = div_b(i, r), o = i - r.st[k];
   int64_t acc = (int64_t)t.pre[k * S + s];
   uint32_t l = 0;
   for (uint32_t step = 0; step < 4 * t.L + 4; step++) {
@@ -248,13 +286,9 @@ __device__ uint64_t q_rank(const TreeView& t, uint32_t c, uint64_t i) {
     uint64_t len = qlen(t, v, k);
     if (o == len) return (uint64_t)(acc + cget(v.cnt, v.cw, k * S + s));
     if (qmarked(v, k)) {
-      if (l + 1 == t.L) {
-        const uint8_t* p = t.leaf + qrank(v, k) * v.b;
-        for (uint64_t x = 0; x < o; x++) acc += p[x] == (c & 0xFF);
-        return (uint64_t)acc;
-      }
+      if (l + 1 == t.L) return (uint64_t)(acc + leaf_count(t.leaf + qrank(v, k) * v.b, o, c & 0xFF));
       const LevelView& w = t.lv[l + 1];
-      uint64_t j = o / w.b, f = qrank(v, k) * v.arity;
+      uint64_t j = div_b(o, w), f = qrank(v, k) * v.arity;
       for (uint64_t x = 0; x < j; x++) acc += cget(w.cnt, w.cw, (f + x) * S + s);
       o -= j * w.b;
       k = f + j;
@@ -296,11 +330,8 @@ __device__ uint64_t q_select(const TreeView& t, uint32_t c, uint64_t j) {
     const LevelView& v = t.lv[l];
     if (qmarked(v, k)) {
       if (l + 1 == t.L) {
-        const uint8_t* p = t.leaf + qrank(v, k) * v.b;
-        uint64_t len = qlen(t, v, k);
-        for (uint64_t x = 0; x < len; x++)
-          if (p[x] == (c & 0xFF) && --j == 0) return (uint64_t)(res + (int64_t)x);
-        return kNone;
+        const uint64_t x = leaf_find(t.leaf + qrank(v, k) * v.b, qlen(t, v, k), c & 0xFF, j);
+        return x == kNone ? kNone : (uint64_t)(res + (int64_t)x);
       }
       const LevelView& w = t.lv[l + 1];
       uint64_t f = qrank(v, k) * v.arity, i = 0;
@@ -329,9 +360,93 @@ __device__ uint64_t q_select(const TreeView& t, uint32_t c, uint64_t j) {
   return kNone;
 }
 
-__global__ void k_queries(const TreeView* __restrict__ tv, int kind, const uint64_t* __restrict__ args,
-                          uint64_t m, uint64_t* __restrict__ out) {
-  const TreeView& t = *tv;
+// The batched query kernel.  Every CTA first copies the tree's level table
+// and the arrays of its top levels (block starts, marks, rank prefix,
+// pointers, offsets, and the counters while they fit) into shared memory:
+// every query descends through the top levels, so those steps read shared
+// memory instead of L2.  Then each thread answers queries (grid-stride).
+constexpr uint32_t kQThreads = 256;
+
+__device__ __forceinline__ void copy_words(uint32_t* dst, const void* src, uint64_t bytes) {
+  const uint32_t* s = (const uint32_t*)src;
+  for (uint64_t i = threadIdx.x; i < bytes / 4; i += blockDim.x) dst[i] = s[i];
+}
+
+template <uint32_t kQCacheBytes, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_queries(const TreeView* __restrict__ tv, int kind,
+                                                            const uint64_t* __restrict__ args, uint64_t m,
+                                                            uint64_t* __restrict__ out) {
+  if (kQCacheBytes == 0) {  // the level table straight from global memory (L1-cached broadcasts)
+    const TreeView& t = *tv;
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < m;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+      uint64_t r;
+      if (kind == BT_Q_ACCESS) r = q_access(t, args[q]);
+      else if (kind == BT_Q_RANK) r = args[2 * q] > 255 ? kNone : q_rank(t, (uint32_t)args[2 * q], args[2 * q + 1]);
+      else r = args[2 * q] > 255 ? kNone : q_select(t, (uint32_t)args[2 * q], args[2 * q + 1]);
+      out[q] = r;
+    }
+    return;
+  }
+  __shared__ TreeView st;
+  __shared__ __align__(16) uint32_t cache[kQCacheBytes / 4 + 4];
+  __shared__ uint32_t s_off[kMaxLevels][7];
+  __shared__ uint32_t s_lc;
+  {
+    const uint32_t* src = (const uint32_t*)tv;
+    uint32_t* dst = (uint32_t*)&st;
+    for (uint32_t i = threadIdx.x; i < sizeof(TreeView) / 4; i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // Top levels that fit: st, mw, mr, ptr, off, cnt, pc (each 16-byte
+    // aligned in the cache); counters only while the whole level fits.
+    uint32_t used = 0, lc = 0;
+    for (uint32_t l = 0; l < st.L; l++) {
+      const LevelView& v = st.lv[l];
+      const uint64_t words = (v.c + 31) / 32;
+      const uint64_t sz[7] = {v.c * 8, words * 4, (words + 1) * 4, v.c * 4, v.c * 8,
+                              v.c * st.S * v.cw, v.c * st.S * v.cw};
+      uint64_t tot = 0;
+      for (int a = 0; a < 7; a++) tot += (sz[a] + 15) & ~15ull;
+      if (used + tot > kQCacheBytes) break;
+      for (int a = 0; a < 7; a++) {
+        s_off[l][a] = used;
+        used += (uint32_t)((sz[a] + 15) & ~15ull);
+      }
+      lc = l + 1;
+    }
+    s_lc = lc;
+  }
+  __syncthreads();
+  const uint32_t lc = s_lc;
+  for (uint32_t l = 0; l < lc; l++) {
+    const LevelView& v = st.lv[l];
+    const uint64_t words = (v.c + 31) / 32;
+    copy_words(cache + s_off[l][0] / 4, v.st, v.c * 8);
+    copy_words(cache + s_off[l][1] / 4, v.mw, (words * 4 + 3) & ~3ull);
+    copy_words(cache + s_off[l][2] / 4, v.mr, (words + 1) * 4);
+    copy_words(cache + s_off[l][3] / 4, v.ptr, v.c * 4);
+    copy_words(cache + s_off[l][4] / 4, v.off, v.c * 8);
+    const uint64_t cb = (v.c * st.S * v.cw + 3) & ~3ull;
+    copy_words(cache + s_off[l][5] / 4, v.cnt, cb);
+    copy_words(cache + s_off[l][6] / 4, v.pc, cb);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (uint32_t l = 0; l < lc; l++) {
+      LevelView& v = st.lv[l];
+      char* b = (char*)cache;
+      v.st = (const uint64_t*)(b + s_off[l][0]);
+      v.mw = (const uint32_t*)(b + s_off[l][1]);
+      v.mr = (const uint32_t*)(b + s_off[l][2]);
+      v.ptr = (const uint32_t*)(b + s_off[l][3]);
+      v.off = (const uint64_t*)(b + s_off[l][4]);
+      v.cnt = b + s_off[l][5];
+      v.pc = b + s_off[l][6];
+    }
+  __syncthreads();
+  const TreeView& t = st;
   for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < m;
        q += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t r;
@@ -438,7 +553,7 @@ int upload_view(bt_tree* t, cudaStream_t s) {
   h.S = t->S;
   for (uint32_t l = 0; l < t->L; l++) {
     const Level& v = t->lv[l];
-    h.lv[l] = LevelView{v.c, v.b, v.arity, v.st, v.mw, v.mr, v.ptr, v.off, v.cnt, v.pc, v.cw};
+    h.lv[l] = LevelView{v.c, v.b, v.arity, block_shift(v.b), v.st, v.mw, v.mr, v.ptr, v.off, v.cnt, v.pc, v.cw};
   }
   h.pre = t->pre;
   h.leaf = t->leaf;
@@ -452,7 +567,16 @@ int upload_view(bt_tree* t, cudaStream_t s) {
 int run_queries(const bt_tree* t, int kind, const uint64_t* d_args, uint64_t m, uint64_t* d_out,
                 cudaStream_t s) {
   if (m == 0) return BT_OK;
-  BT_LAUNCH(k_queries<<<grid_for(m, 128, 152 * 64), 128, 0, s>>>(t->view, kind, d_args, m, d_out));
+  // Enough CTAs to fill the device (each pays for its shared-memory copy of
+  // the top levels once), threads striding over the queries.
+  // Access descends with few loads per level and gains most from threads in
+  // flight: 128-thread CTAs without the shared-memory copy.  Rank and select
+  // read counters at every level and gain from the copy of the top levels.
+  if (kind == BT_Q_ACCESS)
+    BT_LAUNCH(k_queries<0, 128, 1><<<grid_for(m, 128, 152 * 64), 128, 0, s>>>(t->view, kind, d_args, m, d_out));
+  else
+    BT_LAUNCH(k_queries<12 << 10, kQThreads, 6><<<grid_for(m, kQThreads, 152 * 6), kQThreads, 0, s>>>(
+        t->view, kind, d_args, m, d_out));
   BT_CUDA(cudaGetLastError());
   return BT_OK;
 }
