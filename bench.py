@@ -603,6 +603,17 @@ def run_ours(args):
     blob = bt.bt_export(h)
     queries = measure_queries(bt, torch, stream, h, text) if rank == 0 else None
     bt.bt_free(h)
+    compact = None
+    if rank == 0:
+        # Space-efficient rank/select support: no stored counters on the last
+        # level (counted in the leaf text by the queries that need them).
+        oc = bt.BuildOptions(prune=True, leaf_counts=True, **w.get("opts", {})).to_c()[0]
+        hc = bt.bt_build_ex(d_text, n, w["sigma"], w["tau"], w["leaf"], oc, stream)
+        cbytes = bt.bt_device_bytes(hc)
+        compact = {"tree_device_bytes": cbytes, "default_tree_device_bytes": tree_bytes,
+                   "ratio": cbytes / tree_bytes, "same_export": bt.bt_export(hc) == blob,
+                   "queries": measure_queries(bt, torch, stream, hc, text)}
+        bt.bt_free(hc)
     pinned = torch.from_numpy(text).pin_memory()
     barrier()
     e2 = torch.cuda.Event(enable_timing=True)
@@ -658,6 +669,7 @@ def run_ours(args):
         "build_roofline": build_roofline,
         "int_roofline": int_roof,
         "queries": queries,
+        "leaf_counts": compact,
         "kernels_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n,
                 "d2h_bytes_per_step": d2h},

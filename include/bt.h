@@ -98,8 +98,16 @@ typedef struct {
 /* BT_FLAG_BATCH_WORKERS makes bt_build_batch build every document with
  * bt_build_ex on host worker threads instead of the persistent batched kernel
  * (the comparison arm of the batched build; the same trees). */
+/* BT_FLAG_LEAF_COUNTS: space-efficient rank/select support (the paper's
+ * section 6 names the auxiliary space of rank and select as future work).
+ * The last level, which holds most blocks, stores no per-block symbol
+ * counters: a query that needs one counts it in the leaf text (the block's
+ * own text when marked, the at most two marked blocks its pointer copies
+ * from otherwise; at most 2 leaf_len bytes).  Same tree and same answers,
+ * fewer device bytes, slower rank and select at the last level.  Single-text
+ * builds only (bt_build_batch ignores it). */
 enum { BT_FLAG_DENSE_SCAN = 1, BT_FLAG_TINY_QUEUE = 2, BT_FLAG_GRAM_LIST = 4, BT_FLAG_TWO_PHASE = 8,
-       BT_FLAG_BATCH_WORKERS = 16 };
+       BT_FLAG_BATCH_WORKERS = 16, BT_FLAG_LEAF_COUNTS = 32 };
 
 void bt_opts_default(bt_opts* opts);
 

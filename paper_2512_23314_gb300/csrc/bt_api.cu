@@ -228,6 +228,7 @@ static int build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, 
   ctx.tiny_queue = (o.flags & BT_FLAG_TINY_QUEUE) ? 1 : 0;
   ctx.force_list = (o.flags & BT_FLAG_GRAM_LIST) ? 1 : 0;
   ctx.two_phase = (o.flags & BT_FLAG_TWO_PHASE) ? 1 : 0;
+  ctx.leaf_counts = (o.flags & BT_FLAG_LEAF_COUNTS) ? 1 : 0;
   BT_TRY(sc.alloc(&ctx.st, 1));
   BT_CUDA(cudaMemsetAsync(ctx.st, 0, sizeof(Status), s));
   BT_CUDA(cudaMallocHost(&ctx.st_host, sizeof(Status)));
@@ -274,7 +275,7 @@ static int build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, 
   uint64_t bytes = t->leaf_bytes + 16 + sizeof(TreeView) + 512 + (t->lv[0].c + 1) * t->S * 8;
   for (const Level& v : t->lv) {
     const uint64_t words = (v.c + 31) / 32;
-    bytes += v.c * (8 + 4 + 8) + (2 * words + 1) * 4 + 2 * v.c * t->S * v.cw;
+    bytes += v.c * (8 + 4 + 8) + (2 * words + 1) * 4 + (v.cnt ? 2 * v.c * t->S * v.cw : 0);
   }
   t->dev_bytes = bytes;
   BT_CUDA(cudaStreamSynchronize(s));

@@ -362,6 +362,7 @@ struct BuildCtx {
   int tiny_queue = 0;  // test hook: a 64-entry candidate queue (forces the overflow path)
   int force_list = 0;  // test hook: build the selected-gram list for any text length
   int two_phase = 0;   // BT_FLAG_TWO_PHASE: test every level's windows in two phases
+  int leaf_counts = 0; // BT_FLAG_LEAF_COUNTS: no stored counters on the last level
   // Selected-gram list of the whole text (built once when levels can use it):
   // chunk j of 128 positions lists its grams at gl_chunk[j] .. gl_chunk[j+1].
   const uint32_t* gl_chunk = nullptr;

@@ -219,11 +219,11 @@ __device__ __forceinline__ uint64_t qlen(const TreeView& t, const LevelView& v, 
 // (a per-byte compare, __vcmpeq4, then a population count).
 __device__ __forceinline__ uint64_t leaf_count(const uint8_t* p, uint64_t o, uint32_t c) {
   uint64_t x = 0, acc = 0;
-  if ((((uintptr_t)p) & 3) == 0) {
-    const uint32_t cc = c * 0x01010101u;
-    const uint32_t* w = (const uint32_t*)p;
-    for (; x + 4 <= o; x += 4) acc += __popc(__vcmpeq4(w[x >> 2], cc)) >> 3;
-  }
+  for (; x < o && (((uintptr_t)(p + x)) & 3); x++) acc += p[x] == c;  // up to an aligned word
+  const uint32_t cc = c * 0x01010101u;
+  const uint32_t* w = (const uint32_t*)(p + x);
+  uint64_t i = 0;
+  for (; x + 4 <= o; x += 4, i++) acc += __popc(__vcmpeq4(w[i], cc)) >> 3;
   for (; x < o; x++) acc += p[x] == c;
   return acc;
 }
@@ -249,6 +249,37 @@ __device__ __forceinline__ uint64_t leaf_find(const uint8_t* p, uint64_t len, ui
 // x / b for the block length of a level (a shift when b is a power of two).
 __device__ __forceinline__ uint64_t div_b(uint64_t x, const LevelView& v) {
   return v.bshift != 0xFFu ? x >> v.bshift : x / v.b;
+}
+
+// Space-efficient counters (BT_FLAG_LEAF_COUNTS): the last level stores no
+// symbol counters; they are counted in the leaf text when a query needs them.
+// A marked last-level block's text is its leaf text; an unmarked one copies a
+// window of at most two marked blocks (its target and the next one), whose
+// text is in the leaf text too.
+__device__ uint64_t leaf_block_count(const TreeView& t, const LevelView& v, uint64_t k, uint32_t c) {
+  const uint64_t len = qlen(t, v, k);
+  if (qmarked(v, k)) return leaf_count(t.leaf + qrank(v, k) * v.b, len, c);
+  const uint64_t j = v.ptr[k], o = v.off[k], lj = qlen(t, v, j);
+  const uint64_t first = o + len <= lj ? len : lj - o;
+  uint64_t acc = leaf_count(t.leaf + qrank(v, j) * v.b + o, first, c);
+  if (first < len) acc += leaf_count(t.leaf + qrank(v, j + 1) * v.b, len - first, c);
+  return acc;
+}
+
+// Counts of byte c in T[st[ptr], st[ptr] + off) of an unmarked last-level block.
+__device__ uint64_t leaf_prefix_count(const TreeView& t, const LevelView& v, uint64_t k, uint32_t c) {
+  const uint64_t j = v.ptr[k];
+  return leaf_count(t.leaf + qrank(v, j) * v.b, v.off[k], c);
+}
+
+// Counter of symbol s (byte c) of block k: stored, or counted in the leaf text.
+__device__ __forceinline__ uint64_t blk_cnt(const TreeView& t, const LevelView& v, uint64_t k, uint32_t s,
+                                            uint32_t c) {
+  return v.cnt ? cget(v.cnt, v.cw, k * t.S + s) : leaf_block_count(t, v, k, c);
+}
+__device__ __forceinline__ uint64_t blk_pc(const TreeView& t, const LevelView& v, uint64_t k, uint32_t s,
+                                           uint32_t c) {
+  return v.pc ? cget(v.pc, v.cw, k * t.S + s) : leaf_prefix_count(t, v, k, c);
 }
 
 __device__ uint64_t q_access(const TreeView& t, uint64_t i) {
@@ -284,24 +315,24 @@ __device__ uint64_t q_rank(const TreeView& t, uint32_t c, uint64_t i) {
     const LevelView& v = t.lv[l];
     if (o == 0) return (uint64_t)acc;
     uint64_t len = qlen(t, v, k);
-    if (o == len) return (uint64_t)(acc + cget(v.cnt, v.cw, k * S + s));
+    if (o == len) return (uint64_t)(acc + blk_cnt(t, v, k, s, c & 0xFF));
     if (qmarked(v, k)) {
       if (l + 1 == t.L) return (uint64_t)(acc + leaf_count(t.leaf + qrank(v, k) * v.b, o, c & 0xFF));
       const LevelView& w = t.lv[l + 1];
       uint64_t j = div_b(o, w), f = qrank(v, k) * v.arity;
-      for (uint64_t x = 0; x < j; x++) acc += cget(w.cnt, w.cw, (f + x) * S + s);
+      for (uint64_t x = 0; x < j; x++) acc += blk_cnt(t, w, f + x, s, c & 0xFF);
       o -= j * w.b;
       k = f + j;
       l++;
     } else {
       uint64_t P = v.ptr[k], x = v.off[k] + o;
-      acc -= cget(v.pc, v.cw, k * S + s);
+      acc -= blk_pc(t, v, k, s, c & 0xFF);
       uint64_t lp = qlen(t, v, P);
       if (x <= lp) {
         k = P;
         o = x;
       } else {
-        acc += cget(v.cnt, v.cw, P * S + s);
+        acc += blk_cnt(t, v, P, s, c & 0xFF);
         k = P + 1;
         o = x - lp;
       }
@@ -335,8 +366,10 @@ __device__ uint64_t q_select(const TreeView& t, uint32_t c, uint64_t j) {
       }
       const LevelView& w = t.lv[l + 1];
       uint64_t f = qrank(v, k) * v.arity, i = 0;
-      while (i < v.arity && cget(w.cnt, w.cw, (f + i) * S + s) < j) {
-        j -= cget(w.cnt, w.cw, (f + i) * S + s);
+      while (i < v.arity) {
+        const uint64_t cc = blk_cnt(t, w, f + i, s, c & 0xFF);
+        if (cc >= j) break;
+        j -= cc;
         i++;
       }
       if (i == v.arity) return kNone;
@@ -344,8 +377,8 @@ __device__ uint64_t q_select(const TreeView& t, uint32_t c, uint64_t j) {
       k = f + i;
       l++;
     } else {
-      uint64_t P = v.ptr[k], jj = j + cget(v.pc, v.cw, k * S + s);
-      const uint32_t cp = cget(v.cnt, v.cw, P * S + s);
+      uint64_t P = v.ptr[k], jj = j + blk_pc(t, v, k, s, c & 0xFF);
+      const uint64_t cp = blk_cnt(t, v, P, s, c & 0xFF);
       if (jj <= cp) {
         res -= (int64_t)v.off[k];
         k = P;
@@ -405,8 +438,8 @@ __global__ void __launch_bounds__(NT, MINB) k_queries(const TreeView* __restrict
     for (uint32_t l = 0; l < st.L; l++) {
       const LevelView& v = st.lv[l];
       const uint64_t words = (v.c + 31) / 32;
-      const uint64_t sz[7] = {v.c * 8, words * 4, (words + 1) * 4, v.c * 4, v.c * 8,
-                              v.c * st.S * v.cw, v.c * st.S * v.cw};
+      const uint64_t cb = v.cnt ? v.c * st.S * v.cw : 0;
+      const uint64_t sz[7] = {v.c * 8, words * 4, (words + 1) * 4, v.c * 4, v.c * 8, cb, cb};
       uint64_t tot = 0;
       for (int a = 0; a < 7; a++) tot += (sz[a] + 15) & ~15ull;
       if (used + tot > kQCacheBytes) break;
@@ -428,9 +461,11 @@ __global__ void __launch_bounds__(NT, MINB) k_queries(const TreeView* __restrict
     copy_words(cache + s_off[l][2] / 4, v.mr, (words + 1) * 4);
     copy_words(cache + s_off[l][3] / 4, v.ptr, v.c * 4);
     copy_words(cache + s_off[l][4] / 4, v.off, v.c * 8);
-    const uint64_t cb = (v.c * st.S * v.cw + 3) & ~3ull;
-    copy_words(cache + s_off[l][5] / 4, v.cnt, cb);
-    copy_words(cache + s_off[l][6] / 4, v.pc, cb);
+    if (v.cnt) {
+      const uint64_t cb = (v.c * st.S * v.cw + 3) & ~3ull;
+      copy_words(cache + s_off[l][5] / 4, v.cnt, cb);
+      copy_words(cache + s_off[l][6] / 4, v.pc, cb);
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0)
@@ -442,8 +477,10 @@ __global__ void __launch_bounds__(NT, MINB) k_queries(const TreeView* __restrict
       v.mr = (const uint32_t*)(b + s_off[l][2]);
       v.ptr = (const uint32_t*)(b + s_off[l][3]);
       v.off = (const uint64_t*)(b + s_off[l][4]);
-      v.cnt = b + s_off[l][5];
-      v.pc = b + s_off[l][6];
+      if (v.cnt) {
+        v.cnt = b + s_off[l][5];
+        v.pc = b + s_off[l][6];
+      }
     }
   __syncthreads();
   const TreeView& t = st;
@@ -484,8 +521,17 @@ int build_counters(BuildCtx& ctx) {
   const uint32_t S = t->S;
   const unsigned T = 256;
   const size_t smem = 8 * S * sizeof(unsigned int);
+  // Space-efficient counters: the last level keeps none (queries count its
+  // blocks in the leaf text), and the marked blocks of the level above are
+  // counted in the text instead of summed from children.
+  const bool leaf_counts = ctx.leaf_counts && t->L >= 2;
   for (int l = (int)t->L - 1; l >= 0; l--) {
     Level& v = t->lv[l];
+    v.cw = counter_width(v.b);
+    if (leaf_counts && l + 1 == (int)t->L) {
+      v.cnt = v.pc = nullptr;
+      continue;
+    }
     // Counters of cw bytes (a count never exceeds b).  Narrow rows are
     // written whole by the kernels; 4-byte rows are accumulated from zero.
     v.cw = counter_width(v.b);
@@ -500,7 +546,8 @@ int build_counters(BuildCtx& ctx) {
     const bool last = l + 1 == (int)t->L;
     CountJob J{v.st, v.ptr, v.off, v.mw, v.c, v.b, t->n, v.cnt, v.cw, 0, 0, 0};
     CountJob P{v.st, v.ptr, v.off, v.mw, v.c, v.b, t->n, v.pc, v.cw, 1, 1, 0};
-    if (!last) J.only_unmarked = 1;  // marked blocks are sums of their children
+    const bool children_counted = !last && !(leaf_counts && l + 2 == (int)t->L);
+    if (children_counted) J.only_unmarked = 1;  // marked blocks are sums of their children
     if (v.cw == 1) {
       // One thread per block; the rows of marked blocks are written as zeros
       // and the sums of children overwrite them below.
@@ -512,7 +559,7 @@ int build_counters(BuildCtx& ctx) {
       BT_LAUNCH(k_count<<<grid_for(v.c * ppb * 32, T), T, smem, s>>>(J, t->sym, ctx.T, S, ppb));
       BT_LAUNCH(k_count<<<grid_for(v.c * ppb * 32, T), T, smem, s>>>(P, t->sym, ctx.T, S, ppb));
     }
-    if (!last) {
+    if (children_counted) {
       const Level& w = t->lv[l + 1];
       BT_LAUNCH(k_sum_children<<<grid_for(v.c * 32, T), T, 0, s>>>(v.c, v.b, t->n, v.st, v.mw, v.mr, v.arity, w.b,
                                                         w.cnt, w.cw, S, v.cnt, v.cw));
