@@ -106,8 +106,16 @@ typedef struct {
  * from otherwise; at most 2 leaf_len bytes).  Same tree and same answers,
  * fewer device bytes, slower rank and select at the last level.  Single-text
  * builds only (bt_build_batch ignores it). */
+/* BT_FLAG_SORT_SCAN: the sort-based level pass of the paper's section 4.1
+ * instead of the table probes: every window of length b (then 2b) inside a
+ * run becomes a (fingerprint, position) tuple, the tuples are radix-sorted
+ * stably, and each block (pair) takes the first position of its
+ * fingerprint's group as its leftmost candidate.  Verification and the rest of
+ * the level are shared with the default path; the same tree.  It moves about
+ * 24 bytes per covered position and sort pass (slower; a second algorithm to
+ * compare with).  Single-text builds only; n * b_l < 2^32 per level. */
 enum { BT_FLAG_DENSE_SCAN = 1, BT_FLAG_TINY_QUEUE = 2, BT_FLAG_GRAM_LIST = 4, BT_FLAG_TWO_PHASE = 8,
-       BT_FLAG_BATCH_WORKERS = 16, BT_FLAG_LEAF_COUNTS = 32 };
+       BT_FLAG_BATCH_WORKERS = 16, BT_FLAG_LEAF_COUNTS = 32, BT_FLAG_SORT_SCAN = 64 };
 
 void bt_opts_default(bt_opts* opts);
 

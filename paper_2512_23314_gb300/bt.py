@@ -25,6 +25,7 @@ BT_FLAG_GRAM_LIST = 4
 BT_FLAG_TWO_PHASE = 8
 BT_FLAG_BATCH_WORKERS = 16
 BT_FLAG_LEAF_COUNTS = 32
+BT_FLAG_SORT_SCAN = 64
 ST_FIELDS = 10
 ST_NAMES = ("nblocks", "b", "cov", "nmarked", "npairs", "verify_bytes", "collisions",
             "final_blocks", "candidates", "hits")
@@ -335,6 +336,7 @@ class BuildOptions:
     batch_workers: bool = False  # bt_build_batch: host workers instead of the batched kernel
     batch_ctas: int = 0  # bt_build_batch: CTAs of the batched kernel's launch (0: every SM)
     leaf_counts: bool = False  # no stored counters on the last level (space-efficient rank/select)
+    sort_scan: bool = False  # leftmost windows by radix-sorting (fingerprint, position) tuples
 
     def to_c(self):
         o = bt_opts_default()
@@ -349,7 +351,8 @@ class BuildOptions:
                    | (BT_FLAG_GRAM_LIST if self.gram_list else 0)
                    | (BT_FLAG_TWO_PHASE if self.two_phase else 0)
                    | (BT_FLAG_BATCH_WORKERS if self.batch_workers else 0)
-                   | (BT_FLAG_LEAF_COUNTS if self.leaf_counts else 0))
+                   | (BT_FLAG_LEAF_COUNTS if self.leaf_counts else 0)
+                   | (BT_FLAG_SORT_SCAN if self.sort_scan else 0))
         keep = None
         if self.level_sizes is not None:
             keep = np.ascontiguousarray(self.level_sizes, dtype=np.uint64)

@@ -229,6 +229,7 @@ static int build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, 
   ctx.force_list = (o.flags & BT_FLAG_GRAM_LIST) ? 1 : 0;
   ctx.two_phase = (o.flags & BT_FLAG_TWO_PHASE) ? 1 : 0;
   ctx.leaf_counts = (o.flags & BT_FLAG_LEAF_COUNTS) ? 1 : 0;
+  ctx.sort_scan = (o.flags & BT_FLAG_SORT_SCAN) ? 1 : 0;
   BT_TRY(sc.alloc(&ctx.st, 1));
   BT_CUDA(cudaMemsetAsync(ctx.st, 0, sizeof(Status), s));
   BT_CUDA(cudaMallocHost(&ctx.st_host, sizeof(Status)));

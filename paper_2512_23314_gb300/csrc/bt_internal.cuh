@@ -349,6 +349,12 @@ int scan_u32(const uint32_t* d_in, uint32_t* d_out, uint64_t n, cudaStream_t s, 
 inline uint64_t scan_scratch_words(uint64_t n) { return (n + 1023) / 1024 + 1; }
 int scan_u64(const uint64_t* d_in, uint64_t* d_out, uint64_t n, cudaStream_t s);
 
+// Stable LSD radix sort of (keys, vals)[0, n) by the low `bits` key bits
+// (bt_sort.cu); (tk, tv) hold n entries each, scratch radix_sort_scratch_words(n).
+uint64_t radix_sort_scratch_words(uint64_t n);
+int radix_sort_u64_u32(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, uint64_t n, uint32_t bits,
+                       uint32_t* scratch, cudaStream_t s);
+
 struct BuildCtx {
   bt_tree* t;
   const uint8_t* T;   // device text
@@ -363,6 +369,7 @@ struct BuildCtx {
   int force_list = 0;  // test hook: build the selected-gram list for any text length
   int two_phase = 0;   // BT_FLAG_TWO_PHASE: test every level's windows in two phases
   int leaf_counts = 0; // BT_FLAG_LEAF_COUNTS: no stored counters on the last level
+  int sort_scan = 0;   // BT_FLAG_SORT_SCAN: leftmost windows by sorting instead of probing
   // Selected-gram list of the whole text (built once when levels can use it):
   // chunk j of 128 positions lists its grams at gl_chunk[j] .. gl_chunk[j+1].
   const uint32_t* gl_chunk = nullptr;

@@ -280,6 +280,96 @@ __global__ void __launch_bounds__(256) k_scan(M m, Geo g, uint64_t cpb,
 }
 
 // ---------------------------------------------------------------------------
+// 3''. The sort-based window pass (BT_FLAG_SORT_SCAN; section 4.1).  Instead
+// of probing the key table with every window, the fingerprints of all windows
+// of a length are written as (fingerprint, position) tuples in text order and
+// sorted stably: equal fingerprints become consecutive, in position order, so
+// the first tuple of a key's group is the leftmost window with the key's
+// fingerprint.  Each key finds its group by binary search.  The minima go to
+// the same table fields the scan fills, and verification, marks, pointers and
+// the split follow unchanged.
+// ---------------------------------------------------------------------------
+template <class M>
+__global__ void k_sort_windows(M m, Geo g, uint64_t L, uint64_t BL, uint32_t bshift, uint64_t* __restrict__ keys,
+                               uint32_t* __restrict__ vals) {
+  const uint64_t total = g.c * g.b;
+  for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < total;
+       w += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = bshift != 0xFFu ? w >> bshift : w / g.b, j = w - k * g.b;
+    uint64_t key = kNone;
+    const uint64_t p = g.st[k] + j;
+    if (j < blen(g, k) && p + L <= avail_end(g, k)) key = window_fast(m, g.H, BL, p, L);
+    keys[w] = key;
+    vals[w] = (uint32_t)p;
+  }
+}
+
+__device__ __forceinline__ uint64_t lower_bound_u64(const uint64_t* __restrict__ a, uint64_t n, uint64_t x) {
+  uint64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) / 2;
+    if (a[mid] < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// pair = 0: every full-length block's slot minimum from the sorted windows of
+// length b; pair = 1: every pair's slot minimum from those of length 2b.
+template <class M>
+__global__ void k_sort_minima(M m, Geo g, int pair, const uint64_t* __restrict__ fpB,
+                              const uint32_t* __restrict__ slotB, const uint32_t* __restrict__ slotP, BSlot* bt,
+                              PSlot* pt, const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                              uint64_t nkeys) {
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < g.c;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t F;
+    unsigned long long* lo;
+    if (!pair) {
+      if (slotB[k] == kNoSlot) continue;
+      F = fpB[k];
+      lo = &bt[slotB[k]].lo;
+    } else {
+      if (k + 1 >= g.c || slotP[k] == kNoSlot || slotP[k] == kTailPair) continue;
+      F = m.add(m.mul(fpB[k], g.Bb), fpB[k + 1]);
+      lo = &pt[slotP[k]].lo;
+    }
+    const uint64_t h = lower_bound_u64(keys, nkeys, F);
+    if (h < nkeys && keys[h] == F) min_pos(lo, vals[h]);
+  }
+}
+
+// The short tail (length r) and the pair ending in it (length b + r): the
+// leftmost window with each fingerprint, a minimum per CTA then one atomic.
+template <class M>
+__global__ void __launch_bounds__(256) k_sort_tail(M m, Geo g, uint32_t bshift, const uint64_t* __restrict__ fpB,
+                                                   const uint32_t* __restrict__ slotP, LevelDev* ld) {
+  __shared__ unsigned long long s_min[2];
+  if (threadIdx.x == 0) s_min[0] = s_min[1] = kNone;
+  __syncthreads();
+  const uint64_t fp_tail = ld->fp_tail;
+  const bool tp = g.c >= 2 && slotP[g.c - 2] == kTailPair;
+  const uint64_t fp_tp = tp ? m.add(m.mul(fpB[g.c - 2], g.Br), fp_tail) : 0;
+  uint64_t m0 = kNone, m1 = kNone;
+  const uint64_t total = g.c * g.b;
+  for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < total;
+       w += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = bshift != 0xFFu ? w >> bshift : w / g.b, j = w - k * g.b;
+    if (j >= blen(g, k)) continue;
+    const uint64_t p = g.st[k] + j, av = avail_end(g, k);
+    if (p < m0 && p + g.r <= av && window_fast(m, g.H, g.Br, p, g.r) == fp_tail) m0 = p;
+    if (tp && p < m1 && p + g.b + g.r <= av && window_fast(m, g.H, g.Bbr, p, g.b + g.r) == fp_tp) m1 = p;
+  }
+  if (m0 != kNone) atomicMin(&s_min[0], (unsigned long long)m0);
+  if (m1 != kNone) atomicMin(&s_min[1], (unsigned long long)m1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_min[0] != kNone) atomicMin(&ld->lo_tail, s_min[0]);
+    if (s_min[1] != kNone) atomicMin(&ld->lo_tailpair, s_min[1]);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // 3'. The anchored window scan.
 //
 // Probing the table at every window position costs a random memory access
@@ -1881,6 +1971,36 @@ int exact_pass(const M& m, const Geo& g, uint64_t cpb, int pair, LevelWork& W, c
   return BT_OK;
 }
 
+// The sort-based pass of a level: sorted windows of length b give the block
+// minima, sorted windows of length 2b the pair minima, a dense pass the two
+// tail keys.
+template <class M>
+int sort_minima(const M& m, const Geo& g, LevelWork& W, uint64_t c, uint64_t b, uint64_t r, cudaStream_t s) {
+  const uint64_t npos = c * b;
+  if (npos >= (1ull << 32)) return BT_EINVAL;
+  const uint32_t bshift = (b & (b - 1)) == 0 ? (uint32_t)__builtin_ctzll(b) : 0xFFu;
+  Scratch sc(s);
+  uint64_t *keys, *tk;
+  uint32_t *vals, *tv, *scr;
+  BT_TRY(sc.alloc(&keys, npos));
+  BT_TRY(sc.alloc(&tk, npos));
+  BT_TRY(sc.alloc(&vals, npos));
+  BT_TRY(sc.alloc(&tv, npos));
+  BT_TRY(sc.alloc(&scr, radix_sort_scratch_words(npos)));
+  const unsigned T = 256;
+  for (int pair = 0; pair < 2; pair++) {
+    const uint64_t L = pair ? 2 * b : b;
+    const uint64_t BL = pair ? m.mul(g.Bb, g.Bb) : g.Bb;
+    BT_LAUNCH(k_sort_windows<M><<<grid_for(npos, T), T, 0, s>>>(m, g, L, BL, bshift, keys, vals));
+    BT_TRY(radix_sort_u64_u32(keys, vals, tk, tv, npos, 64, scr, s));
+    BT_LAUNCH(k_sort_minima<M><<<grid_for(c, T), T, 0, s>>>(m, g, pair, W.fpB, W.slotB, W.slotP, W.bt, W.pt, keys,
+                                                            vals, npos));
+  }
+  if (r) BT_LAUNCH(k_sort_tail<M><<<grid_for(npos, T), T, 0, s>>>(m, g, bshift, W.fpB, W.slotP, W.ld));
+  BT_CUDA(cudaGetLastError());
+  return BT_OK;
+}
+
 template <class M>
 int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
   bt_tree* t = ctx.t;
@@ -1910,7 +2030,7 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
   const unsigned T = 256;
   const unsigned gc = grid_for(c, T);
   const uint64_t words = (c + 31) / 32;
-  const bool anchored = !ctx.dense_scan;
+  const bool anchored = !ctx.dense_scan && !ctx.sort_scan;
   const GramP gp = choose_gram(b, r, c);
   const uint64_t acap = anchored ? pow2_at_least(2 * (c + 2)) : 0;
   GramP gq = gp;
@@ -2009,7 +2129,10 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
   BT_LAUNCH(k_block_fp<M><<<gc, T, 0, s>>>(m, g, W.fpB, W.slotB, W.bt, bcap - 1, W.ld, ctx.st));
   BT_LAUNCH(k_pair_insert<<<gc, T, 0, s>>>(g, W.slotB, W.slotP, W.pt, pcap - 1, W.bt, W.ld,
                                            ctx.st));
-  if (!anchored) {
+  if (ctx.sort_scan) {
+    ProfScope ps("window_scan", s, cov_l);
+    BT_TRY(sort_minima(m, g, W, c, b, r, s));
+  } else if (!anchored) {
     ProfScope ps("window_scan", s, cov_l);
     BT_LAUNCH(k_scan<M><<<grid_for(c * cpb, T), T, 0, s>>>(m, g, cpb, W.bt, bcap - 1, W.pt, pcap - 1,
                                                             W.ld, 0));
