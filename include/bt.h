@@ -161,15 +161,19 @@ int bt_build_batch(const uint8_t* const* texts, const uint64_t* ns, const uint32
                    const bt_opts* opts, uint32_t nworkers, bt_tree** outs);
 
 /* Measurement hooks of the batched build (not part of the paper's method).
- * bt_batch_report: what the last bt_build_batch call of the process did, 11
+ * bt_batch_report: what the last bt_build_batch call of the process did, 13
  * u64: documents built by the batched kernel, documents built by host
  * workers, kernel launches, documents built a second time because the output
  * pool ran out, threads per CTA, CTAs per SM, output pool bytes, CTA scratch
- * bytes, the largest grid, the scan's window chunk (positions per lane and
- * step), and the autotuner's trial builds in this call.  The launch shape
- * (threads, CTAs per SM, chunk) of a batch of 1024 or more documents is
- * chosen by timing each candidate on a seeded sample of the batch the first
- * time a batch of its size class is built, and cached for the process.  bt_batch_cycles: for a tree from the batched
+ * bytes, the largest grid, the scan's window run (consecutive positions per
+ * lane), the autotuner's trial builds in this call, the microseconds the
+ * host spent issuing the texts' copies to the device (the copies themselves
+ * when the texts are in pageable memory) and the microseconds of device time
+ * of the batched kernel's launches.  The launch shape (threads, CTAs per SM,
+ * run) of a batch of 1024 or more documents is chosen the first time a batch
+ * of its size class is built, and cached for the process: each candidate
+ * builds a seeded sample of the batch, and the one whose measured cycles per
+ * byte and level give the shortest simulated batch wins.  bt_batch_cycles: for a tree from the batched
  * kernel, the SM clock cycles its CTA spent per phase (6 u64: set-up,
  * tables, window scan, verification/marks/pointers/split, pruning, output
  * and counters); zeros for other trees.  BT_EINVAL for null pointers or cap

@@ -186,10 +186,10 @@ def bt_build_batch(texts, ns, sigmas, taus, leaf_lens, opts: bt_opts | None = No
 
 def bt_batch_report() -> dict:
     """What the last bt_build_batch call did (measurement hook)."""
-    a = (ctypes.c_uint64 * 11)()
-    _check(lib().bt_batch_report(a, 11), "bt_batch_report")
+    a = (ctypes.c_uint64 * 13)()
+    _check(lib().bt_batch_report(a, 13), "bt_batch_report")
     names = ("kernel_docs", "worker_docs", "launches", "retried", "threads", "ctas_per_sm", "pool_bytes",
-             "scratch_bytes", "max_grid", "chunk", "tuning_trials")
+             "scratch_bytes", "max_grid", "chunk", "tuning_trials", "upload_us", "kernel_us")
     return dict(zip(names, list(a)))
 
 

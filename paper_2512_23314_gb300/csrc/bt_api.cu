@@ -24,7 +24,9 @@ int upload_view(bt_tree* t, cudaStream_t s);
 int batch_kernel_build(const uint8_t* const* texts, const uint64_t* ns, const uint32_t* sigmas,
                        const uint32_t* taus, const uint32_t* leaf_lens, uint64_t ndocs, const bt_opts& o,
                        std::vector<char>& routed, bt_tree** outs, uint32_t threads, uint32_t ctas_per_sm,
-                       uint32_t chunk, cudaStream_t s);
+                       uint32_t chunk, cudaStream_t s, const std::vector<char>* eligible);
+uint32_t batch_split(const uint64_t* ns, const uint32_t* taus, const uint32_t* leaf_lens, uint64_t ndocs,
+                     const bt_opts& o, uint32_t ctas_per_sm, std::vector<char>& eligible);
 int batch_shape(const uint8_t* const* texts, const uint64_t* ns, const uint32_t* sigmas, const uint32_t* taus,
                 const uint32_t* leaf_lens, uint64_t ndocs, const bt_opts& o, cudaStream_t s, uint32_t* threads,
                 uint32_t* ctas_per_sm, uint32_t* chunk, uint64_t* tuned_now);
@@ -402,10 +404,14 @@ int bt_build_batch(const uint8_t* const* texts, const uint64_t* ns, const uint32
   bt_opts o;
   if (opts) o = *opts;
   else bt_opts_default(&o);
-  // The persistent batched kernel takes every document it can; the rest (and
-  // every document with BT_FLAG_BATCH_WORKERS) go to host workers.
+  // The persistent batched kernel takes every document it can, except the
+  // few whose work would outlast the rest of the batch on one CTA: those are
+  // built at the same time by the single-text path on host workers (as is
+  // every document the kernel cannot take, and every document with
+  // BT_FLAG_BATCH_WORKERS).
   std::vector<char> routed(ndocs, 0);
-  int rc = BT_OK;
+  int rc = BT_OK, rc_split = BT_OK;
+  uint64_t split_docs = 0;
   batch_report_reset();
   if (!(o.flags & BT_FLAG_BATCH_WORKERS)) {
     cudaStream_t s;
@@ -419,17 +425,41 @@ int bt_build_batch(const uint8_t* const* texts, const uint64_t* ns, const uint32
     uint32_t threads = 0, ctas = 0, chunk = 0;
     uint64_t trials = 0;
     rc = batch_shape(texts, ns, sigmas, taus, leaf_lens, ndocs, o, s, &threads, &ctas, &chunk, &trials);
-    if (rc == BT_OK) {
+    std::vector<char> eligible;
+    bt_opts ok = o;
+    const uint32_t cap = rc == BT_OK ? batch_split(ns, taus, leaf_lens, ndocs, o, ctas, eligible) : 0;
+    std::thread split_thread;
+    if (cap) {
+      ok.batch_ctas = cap;
+      std::vector<char> not_heavy(ndocs, 1);
+      for (uint64_t d = 0; d < ndocs; d++) {
+        not_heavy[d] = eligible[d];
+        split_docs += !eligible[d];
+      }
+      try {
+        split_thread = std::thread([&, not_heavy]() {
+          cudaSetDevice(device);
+          rc_split = worker_builds(texts, ns, sigmas, taus, leaf_lens, ndocs, opts, nworkers, not_heavy, outs);
+        });
+      } catch (...) {
+        rc_split = BT_ENOMEM;
+      }
+    }
+    if (rc == BT_OK && rc_split == BT_OK) {
       batch_report_reset();
-      rc = batch_kernel_build(texts, ns, sigmas, taus, leaf_lens, ndocs, o, routed, outs, threads, ctas, chunk,
-                              s);
+      rc = batch_kernel_build(texts, ns, sigmas, taus, leaf_lens, ndocs, ok, routed, outs, threads, ctas, chunk,
+                              s, cap ? &eligible : nullptr);
       batch_report_tuned(trials);
     }
+    if (split_thread.joinable()) split_thread.join();
+    if (rc == BT_OK) rc = rc_split;
+    for (uint64_t d = 0; d < ndocs; d++)
+      if (cap && !eligible[d]) routed[d] = 1;  // built by the split workers
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
   }
   if (rc == BT_OK) {
-    uint64_t nw = 0;
+    uint64_t nw = split_docs;
     for (uint64_t d = 0; d < ndocs; d++) nw += !routed[d];
     batch_report_workers(nw);
     rc = worker_builds(texts, ns, sigmas, taus, leaf_lens, ndocs, opts, nworkers, routed, outs);

@@ -35,8 +35,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <memory>
 #include <mutex>
+#include <queue>
 #include <thread>
 #include <vector>
 
@@ -83,8 +85,9 @@ struct Cta {
   uint64_t stats[kBMaxLevels][BT_ST_FIELDS];
   uint64_t last_start;
   // current level
-  uint64_t r, Bb, Br;
+  uint64_t r, Bb, Br, B1;
   uint64_t bmask, pmask;
+  uint64_t rtab[256];  // (a + 1) B^b for every byte a
   uint32_t bshift;
   unsigned long long fp_tail, lo_tail, lo_tailpair;
   uint32_t pretail;
@@ -498,6 +501,7 @@ __device__ void level_pass(const M& m, const BParams& P, const BDoc& D, Cta& C, 
     C.r = len_last < b ? len_last : 0;
     C.Bb = pow_mod(m, P.B, b);
     C.Br = C.r ? pow_mod(m, P.B, C.r) : 0;
+    C.B1 = P.B % m.q();
     C.bmask = bcap - 1;
     C.pmask = pcap - 1;
     C.bshift = (b & (b - 1)) == 0 ? (uint32_t)(__ffsll((long long)b) - 1) : 0xFFu;
@@ -575,6 +579,7 @@ __device__ void level_pass(const M& m, const BParams& P, const BDoc& D, Cta& C, 
   while (fwords < c && fwords < filt_words_max) fwords <<= 1;
   const uint64_t fmask = (uint64_t)fwords * 32 - 1;
   for (uint32_t i = tid; i < fwords; i += nt) filt[i] = 0;
+  for (uint32_t a = tid; a < 256; a += nt) C.rtab[a] = m.mul(a + 1, Bb);
   __syncthreads();
   for (uint64_t k = tid; k < c; k += nt)
     if (W.slotB[k] != kNoSlot) {
@@ -585,12 +590,11 @@ __device__ void level_pass(const M& m, const BParams& P, const BDoc& D, Cta& C, 
   tmark(C, 1);
 
   // The window scan: every window [p, p+b) inside a run (and [p, p+r) for the
-  // short tail).  When b is a multiple of 32, a warp takes CH = 32 U
+  // short tail).  When b is a multiple of 32, a warp takes CH = 32 Re
   // consecutive positions of one block (block, run end and bounds are warp
-  // values, positions 32-bit): lane l tests p0 + l + 32 u for u < U, its
-  // prefix-fingerprint loads coalesced with the other lanes' and all in
-  // flight together.  Otherwise every thread maps its positions to blocks
-  // itself.  The short tail's windows are tested only where their first four
+  // values, positions 32-bit) and lane l the Re positions from p0 + l Re,
+  // rolling the fingerprint from one to the next.  Otherwise every thread
+  // maps its positions to blocks itself.  The short tail's windows are tested only where their first four
   // bytes equal the tail's.
   {
     const uint32_t pretail = C.pretail, bshift = C.bshift;
@@ -605,13 +609,20 @@ __device__ void level_pass(const M& m, const BParams& P, const BDoc& D, Cta& C, 
     }
     const ScanArgs A{H, W.bt, W.pt, bmask, pmask, b, r, Bb, Br, fp_tail, pretail, &C.lo_tailpair};
     if (b % 32 == 0) {
-      constexpr int U = 4;
-      const uint32_t Umax = P.scan_u && P.scan_u < (uint32_t)U ? P.scan_u : (uint32_t)U;
-      const uint32_t Ue = b / 32 < Umax ? (uint32_t)(b / 32) : Umax;  // positions per lane
-      const uint32_t CH = 32 * Ue;
+      // A lane takes a run of Re consecutive positions: the first window's
+      // fingerprint comes from two prefix fingerprints, each next one rolls
+      // in one step from the text bytes, phi(p+1, p+1+b) = B phi(p, p+b) +
+      // (T[p+b] + 1) - (T[p] + 1) B^b (the last term from a table in shared
+      // memory), so the loads per window are a few text bytes.
+      constexpr int R = 8;
+      const uint32_t Rmax = P.scan_u && P.scan_u < (uint32_t)R ? P.scan_u : (uint32_t)R;
+      const uint32_t Re = b / 32 < Rmax ? (uint32_t)(b / 32) : Rmax;  // positions per lane
+      const uint32_t CH = 32 * Re;
       const uint64_t cpb = (b + CH - 1) / CH;
       const unsigned lane = tid & 31, nw = nt >> 5;
       const uint8_t* T = D.T;
+      const uint64_t B1 = C.B1;
+      const uint64_t* rtab = C.rtab;
       // Every block of the level present: block k starts at k b and its run
       // ends at min(n, (k + 3) b), with no loads.
       const bool all_present = c == (n + b - 1) / b;
@@ -633,37 +644,46 @@ __device__ void level_pass(const M& m, const BParams& P, const BDoc& D, Cta& C, 
           }
         }
         const uint64_t send = s + (n - s < b ? n - s : b);
-        const uint32_t p0 = (uint32_t)(s + jc * CH);
-        if (p0 >= send) continue;
-        const uint32_t pend = (uint32_t)(p0 + CH < send ? p0 + CH : send);
-        uint64_t x[U], hb[U];
-        bool full[U];
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-          const uint32_t p = p0 + lane + 32u * u;
-          full[u] = u < (int)Ue && p < pend && p + b <= av;
-          if (full[u]) {
-            hb[u] = H[p + b];
-            x[u] = H[p];
-          }
+        const uint32_t p = (uint32_t)(s + jc * CH + lane * Re);
+        if (p >= send) continue;
+        const uint32_t pend = (uint32_t)(p + Re < send ? p + Re : send);
+        // Text bytes [p, p+12) and [p+b, p+b+8) from aligned words (a
+        // document's bytes are followed by at least 48 readable bytes).
+        const uint32_t* wa = (const uint32_t*)(T + (p & ~3u));
+        const uint32_t sa = 8 * (p & 3);
+        const uint32_t a0 = wa[0], a1 = wa[1], a2 = wa[2];
+        const uint32_t ta0 = __funnelshift_r(a0, a1, sa), ta1 = __funnelshift_r(a1, a2, sa);
+        uint32_t ta2 = 0;
+        if (r) ta2 = __funnelshift_r(a2, wa[3], sa);
+        const bool full0 = p + b <= av;
+        uint64_t x = 0;
+        uint32_t tb0 = 0, tb1 = 0;
+        if (full0) {
+          const uint32_t q = p + (uint32_t)b;
+          const uint32_t* wb = (const uint32_t*)(T + (q & ~3u));
+          const uint32_t sb = 8 * (q & 3);
+          const uint32_t b0 = wb[0], b1 = wb[1], b2 = wb[2];
+          tb0 = __funnelshift_r(b0, b1, sb);
+          tb1 = __funnelshift_r(b1, b2, sb);
+          x = m.sub(H[q], m.mul(H[p], Bb));
         }
 #pragma unroll
-        for (int u = 0; u < U; u++)
-          if (full[u]) {
-            x[u] = m.sub(hb[u], m.mul(x[u], Bb));
-            const uint64_t bit = x[u] & fmask;
-            if ((filt[bit >> 5] >> (bit & 31)) & 1u) window_hit(m, A, p0 + lane + 32u * u, av, x[u], hb[u]);
-          }
-        if (r) {
-          // Four text bytes at each lane's positions, from aligned words.
-#pragma unroll
-          for (int u = 0; u < U; u++) {
-            const uint32_t p = p0 + lane + 32u * u;
-            if (u < (int)Ue && p < pend && p + r <= av) {
-              const uint32_t* w4 = (const uint32_t*)(T + (p & ~3u));
-              const uint32_t v = __funnelshift_r(w4[0], w4[1], 8 * (p & 3));
-              if ((v & tail4_mask) == tail4 && phi(m, H, Br, p, r) == fp_tail) min_pos(&C.lo_tail, p);
+        for (int i = 0; i < R; i++) {
+          if (i >= (int)Re) break;
+          const uint32_t q = p + i;
+          if (q >= pend) break;
+          if (q + b <= av) {
+            const uint64_t bit = x & fmask;
+            if ((filt[bit >> 5] >> (bit & 31)) & 1u) window_hit(m, A, q, av, x, H[q + b]);
+            if (i + 1 < R) {
+              const uint32_t lo = i < 4 ? ta0 : ta1, ins = i < 4 ? tb0 : tb1;
+              const uint32_t sh = 8 * (i & 3);
+              x = m.sub(m.add(m.mul(x, B1), ((ins >> sh) & 0xFFu) + 1), rtab[(lo >> sh) & 0xFFu]);
             }
+          }
+          if (r && q + r <= av) {
+            const uint32_t v = i < 4 ? __funnelshift_r(ta0, ta1, 8 * (i & 3)) : __funnelshift_r(ta1, ta2, 8 * (i & 3));
+            if ((v & tail4_mask) == tail4 && phi(m, H, Br, q, r) == fp_tail) min_pos(&C.lo_tail, q);
           }
         }
       }
@@ -1378,7 +1398,7 @@ __global__ void __launch_bounds__(NT, MINB) k_batch(BParams P, M m) {
 // What the last batched build did (bt_batch_report).
 struct Report {
   uint64_t kernel_docs, worker_docs, launches, retried, threads, ctas_per_sm, pool_bytes, scratch_bytes,
-      max_grid, chunk, tuned;
+      max_grid, chunk, tuned, upload_us, kernel_us;
 };
 std::mutex g_report_mu;
 Report g_report{};
@@ -1506,8 +1526,11 @@ int run_batch(const M& m, const uint8_t* const* texts, const uint32_t* taus, con
   }
   uint8_t* d_text;
   BT_TRY(mem.alloc(&d_text, ttotal + 64));
+  const auto t_up = std::chrono::steady_clock::now();
   for (uint64_t k = 0; k < nd; k++)
     BT_CUDA(cudaMemcpyAsync(d_text + toff[k], texts[plans[k].i], plans[k].n, cudaMemcpyDefault, s));
+  const uint64_t upload_us = (uint64_t)std::chrono::duration_cast<std::chrono::microseconds>(
+                                 std::chrono::steady_clock::now() - t_up).count();
   // Documents in processing order, block sizes, results.
   std::vector<BDoc> hd(nd);
   uint64_t nlv = 0;
@@ -1630,14 +1653,29 @@ int run_batch(const M& m, const uint8_t* const* texts, const uint32_t* taus, con
   }
   char* d_scratch;
   BT_TRY(mem.alloc(&d_scratch, scratch_max));
-  for (size_t ci = 0; ci < cls.size(); ci++)
-    BT_TRY(launch_docs(m, P, order, cls[ci].first, cls[ci].count, threads, ctas_per_sm, cls[ci].grid,
-                       cls[ci].per_cta, d_scratch, d_next + (ci % 64), s));
+  // The launches' device time (measurement hook), between two events.
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  const bool timed = cudaEventCreate(&ev[0]) == cudaSuccess && cudaEventCreate(&ev[1]) == cudaSuccess;
+  if (timed) cudaEventRecord(ev[0], s);
+  int lrc = BT_OK;
+  for (size_t ci = 0; ci < cls.size() && lrc == BT_OK; ci++)
+    lrc = launch_docs(m, P, order, cls[ci].first, cls[ci].count, threads, ctas_per_sm, cls[ci].grid,
+                      cls[ci].per_cta, d_scratch, d_next + (ci % 64), s);
+  if (timed) cudaEventRecord(ev[1], s);
   std::vector<BRes> res(nd);
   std::vector<BLevelRes> lres(nlv);
-  BT_CUDA(cudaMemcpyAsync(res.data(), d_res, nd * sizeof(BRes), cudaMemcpyDeviceToHost, s));
-  BT_CUDA(cudaMemcpyAsync(lres.data(), d_lres, nlv * sizeof(BLevelRes), cudaMemcpyDeviceToHost, s));
-  BT_CUDA(cudaStreamSynchronize(s));
+  if (lrc == BT_OK) {
+    lrc = cudaMemcpyAsync(res.data(), d_res, nd * sizeof(BRes), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+                  cudaMemcpyAsync(lres.data(), d_lres, nlv * sizeof(BLevelRes), cudaMemcpyDeviceToHost, s) ==
+                      cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess
+              ? BT_OK
+              : BT_ECUDA;
+  }
+  float kernel_ms = 0;
+  if (timed && lrc == BT_OK) cudaEventElapsedTime(&kernel_ms, ev[0], ev[1]);
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
+  BT_TRY(lrc);
 
   // Documents whose tree did not fit in the pool: once more, into a pool of
   // the size they reported.
@@ -1747,6 +1785,8 @@ int run_batch(const M& m, const uint8_t* const* texts, const uint32_t* taus, con
   {
     std::lock_guard<std::mutex> g(g_report_mu);
     g_report.kernel_docs = nd;
+    g_report.upload_us = upload_us;
+    g_report.kernel_us = (uint64_t)(kernel_ms * 1000.0f);
     g_report.launches = cls.size();
     g_report.retried = retried;
     g_report.threads = threads;
@@ -1770,7 +1810,7 @@ int run_batch(const M& m, const uint8_t* const* texts, const uint32_t* taus, con
 int batch_kernel_build(const uint8_t* const* texts, const uint64_t* ns, const uint32_t* sigmas,
                        const uint32_t* taus, const uint32_t* leaf_lens, uint64_t ndocs, const bt_opts& o,
                        std::vector<char>& routed, bt_tree** outs, uint32_t threads, uint32_t ctas_per_sm,
-                       uint32_t chunk, cudaStream_t s) {
+                       uint32_t chunk, cudaStream_t s, const std::vector<char>* eligible) {
   if (threads < 64 || threads > kMaxBThreads || threads % 32) return BT_EINVAL;
   if (ctas_per_sm == 0) ctas_per_sm = 1;
   if (o.modulus && (o.modulus < 300 || o.modulus >= (1ull << 32))) return BT_EINVAL;
@@ -1785,6 +1825,7 @@ int batch_kernel_build(const uint8_t* const* texts, const uint64_t* ns, const ui
     std::vector<uint64_t> b;
     BT_TRY(plan_sizes(n, taus[d], leaf_lens[d], o, b));
     if (n > kBMaxText || b.size() > kBMaxLevels) continue;
+    if (eligible && !(*eligible)[d]) continue;
     DocPlan pl;
     pl.i = d;
     pl.n = n;
@@ -1830,7 +1871,7 @@ namespace {
 struct Shape {
   uint32_t threads, ctas, chunk;
 };
-constexpr Shape kShapes[] = {{1024, 1, 4}, {1024, 1, 2}, {512, 1, 4}, {512, 2, 4}};
+constexpr Shape kShapes[] = {{1024, 1, 8}, {1024, 1, 4}, {512, 2, 8}, {512, 2, 4}};
 constexpr uint64_t kTuneMinDocs = 1024;
 std::mutex g_tune_mu;
 std::vector<std::pair<uint64_t, Shape>> g_tuned;
@@ -1891,12 +1932,29 @@ int batch_shape(const uint8_t* const* texts, const uint64_t* ns, const uint32_t*
         stau.push_back(taus[d]);
         sl.push_back(leaf_lens[d]);
       }
+      // A document's work is estimated as its bytes times its levels; a
+      // shape's cost is the batch's makespan when its CTAs, at the cycles
+      // per unit of work measured on the sample, take the documents from the
+      // queue longest first.
+      std::vector<double> work(ndocs, 0.0);
+      double sample_work = 0;
+      {
+        std::vector<uint64_t> b;
+        for (uint64_t d = 0; d < ndocs; d++) {
+          if (ns[d] > kBMaxText || plan_sizes(ns[d], taus[d], leaf_lens[d], o, b) != BT_OK) continue;
+          work[d] = (double)ns[d] * (double)b.size();
+        }
+        for (uint64_t d = 0; d < ndocs; d += step)
+          if (ns[d] <= cap75) sample_work += work[d];
+      }
+      std::vector<double> order(work);
+      std::sort(order.begin(), order.end(), std::greater<double>());
       double best_cost = 1e300;
       for (const Shape& sh : kShapes) {
         std::vector<char> routed;
         std::vector<bt_tree*> outs(st.size(), nullptr);
         const int rc = batch_kernel_build(st.data(), sn.data(), ss.data(), stau.data(), sl.data(), st.size(), o,
-                                          routed, outs.data(), sh.threads, sh.ctas, sh.chunk, s);
+                                          routed, outs.data(), sh.threads, sh.ctas, sh.chunk, s, nullptr);
         cudaStreamSynchronize(s);
         double cycles = 0;
         for (bt_tree* t : outs)
@@ -1904,7 +1962,17 @@ int batch_shape(const uint8_t* const* texts, const uint64_t* ns, const uint32_t*
             for (int i = 0; i < 6; i++) cycles += (double)t->batch_cycles[i];
         for (bt_tree* t : outs) bt_free(t);
         if (rc != BT_OK) return rc;
-        const double cost = cycles / sh.ctas;
+        const double per_work = cycles / std::max(sample_work, 1.0);
+        std::priority_queue<double, std::vector<double>, std::greater<double>> slots;
+        for (uint64_t g = 0; g < (uint64_t)device_sm_count() * sh.ctas; g++) slots.push(0.0);
+        double cost = 0;
+        for (double w : order) {
+          if (w <= 0) break;
+          const double t = slots.top() + w * per_work;
+          slots.pop();
+          slots.push(t);
+          cost = std::max(cost, t);
+        }
         if (cost < best_cost) {
           best_cost = cost;
           best = sh;
@@ -1921,6 +1989,43 @@ int batch_shape(const uint8_t* const* texts, const uint64_t* ns, const uint32_t*
   return BT_OK;
 }
 
+// Long documents are built by the level kernels of the single-text path on
+// host workers, at the same time as the batched kernel builds the others: a
+// document longer than the batch's share per CTA would outlast the batch in
+// its one CTA, and the single-text path's anchored scan gets more out of a
+// long text than one CTA does.  A document is long at kSplitMin bytes or more
+// and at least half the batch's bytes per CTA (so a batch large enough to
+// balance its CTAs is not split).  The batched kernel then leaves the workers
+// a share of the SMs in proportion to the long documents' bytes (at least 8
+// SMs, at most half).  Returns the kernel's CTA cap (0: no split) and clears
+// eligible[d] for the long documents.
+constexpr uint64_t kSplitMin = 8ull << 20;
+
+uint32_t batch_split(const uint64_t* ns, const uint32_t* taus, const uint32_t* leaf_lens, uint64_t ndocs,
+                     const bt_opts& o, uint32_t ctas_per_sm, std::vector<char>& eligible) {
+  (void)taus;
+  (void)leaf_lens;
+  eligible.assign(ndocs, 1);
+  if (ndocs < 64 || o.batch_ctas) return 0;
+  const unsigned nsm = device_sm_count();
+  double total = 0, heavy = 0;
+  for (uint64_t d = 0; d < ndocs; d++) total += (double)ns[d];
+  const double share = total / ((double)nsm * ctas_per_sm);
+  const double lim = std::max((double)kSplitMin, 0.5 * share);
+  for (uint64_t d = 0; d < ndocs; d++)
+    if ((double)ns[d] >= lim) {
+      eligible[d] = 0;
+      heavy += (double)ns[d];
+    }
+  if (heavy == 0 || heavy == total) {
+    eligible.assign(ndocs, 1);
+    return 0;
+  }
+  uint32_t reserve = (uint32_t)((double)nsm * heavy / total + 0.5);
+  reserve = std::max<uint32_t>(8, std::min<uint32_t>(reserve, nsm / 2));
+  return (nsm - reserve) * ctas_per_sm;
+}
+
 void batch_report_tuned(uint64_t trials) {
   std::lock_guard<std::mutex> g(g_report_mu);
   g_report.tuned = trials;
@@ -1930,11 +2035,12 @@ void batch_report_tuned(uint64_t trials) {
 
 extern "C" int bt_batch_report(uint64_t* out, uint32_t cap) {
   using namespace bt;
-  if (!out || cap < 11) return BT_EINVAL;
+  if (!out || cap < 13) return BT_EINVAL;
   std::lock_guard<std::mutex> g(g_report_mu);
-  const uint64_t v[11] = {g_report.kernel_docs, g_report.worker_docs, g_report.launches, g_report.retried,
+  const uint64_t v[13] = {g_report.kernel_docs, g_report.worker_docs, g_report.launches, g_report.retried,
                           g_report.threads, g_report.ctas_per_sm, g_report.pool_bytes, g_report.scratch_bytes,
-                          g_report.max_grid, g_report.chunk, g_report.tuned};
+                          g_report.max_grid, g_report.chunk, g_report.tuned, g_report.upload_us,
+                          g_report.kernel_us};
   memcpy(out, v, sizeof(v));
   return BT_OK;
 }

@@ -169,7 +169,7 @@ struct BParams {
   int prune;
   uint64_t max_rounds;
   uint32_t dyn_words;             // 32-bit words of dynamic shared memory
-  uint32_t scan_u;                // window chunk: positions per lane and step of the scan (1-4)
+  uint32_t scan_u;                // window run: consecutive positions per lane of the scan (1-8)
 };
 
 }  // namespace bt
