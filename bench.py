@@ -332,7 +332,8 @@ def measure_batch(ndocs: int = 8192, min_len: int = 4 << 10, max_len: int = 16 <
                   nworkers: int = 16) -> dict:
     """The batched workload: `ndocs` versioned-text documents of log-uniform
     length (4 KiB - 16 MiB by default: 8192 documents, ~16.5 GB), sigma
-    4-128, tau 2/4/8, leaf 32.  Three arms, texts in host memory in each:
+    4-128, tau 2/4/8, leaf 32.  Three arms, the texts in one pinned host
+    buffer in each (the copy to the device is inside every timed call):
       plain   -- one bt_build_ex call per document, back to back (one
                  document per launch sequence);
       workers -- bt_build_batch with BT_FLAG_BATCH_WORKERS (bt_build_ex on
@@ -346,7 +347,14 @@ def measure_batch(ndocs: int = 8192, min_len: int = 4 << 10, max_len: int = 16 <
     t_gen = time.perf_counter()
     docs = workloads.doc_mix(ndocs, min_len=min_len, max_len=max_len, seed=0xB7EE0004)
     gen_s = time.perf_counter() - t_gen
-    args = ([d.text for d in docs], [len(d.text) for d in docs], [d.sigma for d in docs],
+    pinned = torch.empty(sum(len(d.text) for d in docs), dtype=torch.uint8, pin_memory=True)
+    texts, o = [], 0
+    for d in docs:
+        v = pinned[o:o + len(d.text)]
+        v.copy_(torch.from_numpy(d.text))
+        texts.append(v)
+        o += len(d.text)
+    args = (texts, [len(d.text) for d in docs], [d.sigma for d in docs],
             [d.tau for d in docs], [d.leaf_len for d in docs])
     sample = sorted(np.random.default_rng(7).choice(ndocs, min(64, ndocs), replace=False).tolist())
     o_kernel, _ = bt.BuildOptions().to_c()
@@ -377,7 +385,7 @@ def measure_batch(ndocs: int = 8192, min_len: int = 4 << 10, max_len: int = 16 <
     t0 = time.perf_counter()
     plain_blobs = {}
     for i, d in enumerate(docs):
-        h = bt.bt_build_ex(d.text, len(d.text), d.sigma, d.tau, d.leaf_len)
+        h = bt.bt_build_ex(texts[i], len(d.text), d.sigma, d.tau, d.leaf_len)
         if i in sample:
             plain_blobs[i] = hashlib.sha256(bt.bt_export(h)).hexdigest()
         bt.bt_free(h)
@@ -388,9 +396,10 @@ def measure_batch(ndocs: int = 8192, min_len: int = 4 << 10, max_len: int = 16 <
     phases = ["setup", "tables", "window_scan", "verify_mark_split", "prune", "output_counters"]
     share = (cyc.sum(0) / cyc.sum()).tolist() if cyc.sum() > 0 else None
     return {"workload": f"{ndocs} versioned-text documents, log-uniform {min_len >> 10} KiB - "
-                        f"{max_len >> 20} MiB, sigma 4-128, tau 2/4/8, leaf 32; texts in host memory",
+                        f"{max_len >> 20} MiB, sigma 4-128, tau 2/4/8, leaf 32; texts in pinned host memory",
             "generate_s": gen_s, "docs": ndocs, "bytes": total,
             "docs_per_s": ndocs / kernel_s, "mb_per_s": total / kernel_s / 1e6,
+            "kernel_device_mb_per_s": total / (rep["kernel_us"] * 1e-6) / 1e6 if rep["kernel_us"] else None,
             "workers_docs_per_s": ndocs / workers_s, "plain_docs_per_s": ndocs / plain_s,
             "speedup_vs_plain": plain_s / kernel_s, "speedup_vs_workers": workers_s / kernel_s,
             "workers_mb_per_s": total / workers_s / 1e6, "plain_mb_per_s": total / plain_s / 1e6,
@@ -401,6 +410,36 @@ def measure_batch(ndocs: int = 8192, min_len: int = 4 << 10, max_len: int = 16 <
             "nworkers": nworkers}
 
 
+def measure_sort_variant(bt, torch, stream, d_text, n, w, blob) -> dict:
+    """The sort-based level pass (section 4.1) on the headline text, as one
+    part and in K parts (the domain decomposition of section 4.2), beside the
+    default anchored scan: build time and the peak of the device pool during
+    the build (the working memory).  One warm-up and one timed build each."""
+    out = {"parts": {}}
+
+    def timed(opts):
+        o = bt.BuildOptions(prune=True, **opts, **w.get("opts", {})).to_c()[0]
+        bt.bt_free(bt.bt_build_ex(d_text, n, w["sigma"], w["tau"], w["leaf"], o, stream))
+        torch.cuda.synchronize()
+        bt.bt_device_pool_peak(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h = bt.bt_build_ex(d_text, n, w["sigma"], w["tau"], w["leaf"], o, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        peak = bt.bt_device_pool_peak()
+        same = bt.bt_export(h) == blob
+        bt.bt_free(h)
+        ms = e0.elapsed_time(e1)
+        return {"ms": ms, "mb_per_s": n / (ms * 1e-3) / 1e6, "peak_pool_bytes": peak,
+                "peak_bytes_per_text_byte": peak / n, "same_export": same}
+
+    out["default_anchored"] = timed({})
+    for k in (1, 4, 16):
+        out["parts"][str(k)] = timed({"sort_scan": True, "partitions": k})
+    return out
+
+
 def measure_serve(rate: float = 2000.0, duration: float = 0.5, min_len: int = 1 << 10,
                   max_len: int = 64 << 20, lanes: int = 4) -> dict:
     """The serving loop over the serving workload's full length range (1 KiB -
@@ -408,11 +447,22 @@ def measure_serve(rate: float = 2000.0, duration: float = 0.5, min_len: int = 1 
     document), with a 0.5 s window of Poisson arrivals at 2000 documents/s
     (the 10 s stream would offer ~120 GB of text, too much to generate within
     a bench run).  Documents up to 4 MiB are built in micro-batches by the
-    batched kernel, larger ones alone."""
+    batched kernel, larger ones alone.  The texts arrive in pinned host
+    memory, as a server's receive buffers would hold them."""
+    import torch
+
     from paper_2512_23314_gb300 import serve
     t0 = time.perf_counter()
     arrivals = workloads.serve_arrivals(rate=rate, duration=duration, min_len=min_len,
                                         max_len=max_len)
+    pinned = torch.empty(sum(len(a.doc.text) for a in arrivals), dtype=torch.uint8, pin_memory=True)
+    staged, o = [], 0
+    for a in arrivals:
+        v = pinned[o:o + len(a.doc.text)]
+        v.copy_(torch.from_numpy(a.doc.text))
+        staged.append(workloads.Arrival(a.t, workloads.Doc(v, a.doc.sigma, a.doc.tau, a.doc.leaf_len)))
+        o += len(a.doc.text)
+    arrivals = staged
     gen_s = time.perf_counter() - t0
     srv = serve.Server(hbm_budget=120 << 30, lanes=lanes, queries_per_doc=10_000)
     rep = srv.run(arrivals)
@@ -422,7 +472,7 @@ def measure_serve(rate: float = 2000.0, duration: float = 0.5, min_len: int = 1 
     out["offered_mb_per_s"] = sum(len(a.doc.text) for a in arrivals) / max(duration, 1e-9) / 1e6
     out["workload"] = (f"Poisson {rate:.0f} docs/s for {duration} s ({len(arrivals)} documents), log-uniform "
                        f"{min_len >> 10} KiB - {max_len >> 20} MiB, DNA-like / text-like 50/50, "
-                       f"120 GiB budget, {out['queries_per_doc']} queries per document, {lanes} lanes")
+                       f"120 GiB budget, {out['queries_per_doc']} queries per document, {lanes} lanes; texts in pinned host memory")
     return out
 
 
@@ -614,6 +664,9 @@ def run_ours(args):
                    "ratio": cbytes / tree_bytes, "same_export": bt.bt_export(hc) == blob,
                    "queries": measure_queries(bt, torch, stream, hc, text)}
         bt.bt_free(hc)
+    sort_variant = None
+    if rank == 0 and not args.no_extras:
+        sort_variant = measure_sort_variant(bt, torch, stream, d_text, n, w, blob)
     pinned = torch.from_numpy(text).pin_memory()
     barrier()
     e2 = torch.cuda.Event(enable_timing=True)
@@ -670,6 +723,7 @@ def run_ours(args):
         "int_roofline": int_roof,
         "queries": queries,
         "leaf_counts": compact,
+        "sort_scan": sort_variant,
         "kernels_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n,
                 "d2h_bytes_per_step": d2h},

@@ -76,6 +76,10 @@ typedef struct {
                                   over every SM.  A smaller grid leaves SMs to
                                   other work, e.g. a second batch on another
                                   host thread.                                 */
+  uint32_t partitions;         /* with BT_FLAG_SORT_SCAN: the number K of parts
+                                  of the domain decomposition (section 4.2);
+                                  0 or 1 (default): one part.  Ignored by the
+                                  other passes.                                */
 } bt_opts;
 
 /* flags: BT_FLAG_DENSE_SCAN probes the table at every window position instead
@@ -113,7 +117,15 @@ typedef struct {
  * fingerprint's group as its leftmost candidate.  Verification and the rest of
  * the level are shared with the default path; the same tree.  It moves about
  * 24 bytes per covered position and sort pass (slower; a second algorithm to
- * compare with).  Single-text builds only; n * b_l < 2^32 per level. */
+ * compare with).  Single-text builds only; c_l * b_l < 2^32 per level.
+ * With opts.partitions = K > 1 the windows are taken in K parts of
+ * consecutive windows (the domain decomposition of section 4.2): a part keeps
+ * only its windows whose fingerprint is a key's, sorts them and keeps the
+ * first of each fingerprint; the kept tuples of all parts (at most K per key)
+ * are sorted once more and give the same minima.  Working memory per level:
+ * about 44 bytes per window of a part plus 12 bytes per kept tuple (at most
+ * one per key and part), instead of about 24 bytes per window; two host
+ * synchronisations per part.  The same tree; n < 2^32. */
 enum { BT_FLAG_DENSE_SCAN = 1, BT_FLAG_TINY_QUEUE = 2, BT_FLAG_GRAM_LIST = 4, BT_FLAG_TWO_PHASE = 8,
        BT_FLAG_BATCH_WORKERS = 16, BT_FLAG_LEAF_COUNTS = 32, BT_FLAG_SORT_SCAN = 64 };
 
@@ -307,9 +319,13 @@ int bt_profile_read(bt_profile_entry* out, uint32_t cap, uint32_t* count);
  * the limit.  Process-wide; not for concurrent use with real builds.
  * bt_device_pool_used: bytes currently allocated from the current device's
  * stream-ordered memory pool (the library's builds allocate there), for
- * checking that a failed build gave everything back. */
+ * checking that a failed build gave everything back.
+ * bt_device_pool_peak: the high-water mark of those bytes since the last
+ * reset; reset != 0 then sets the mark to the bytes in use now (a working
+ * memory measurement: reset, build, read). */
 void bt_test_alloc_limit(uint64_t bytes);
 int bt_device_pool_used(uint64_t* out);
+int bt_device_pool_peak(uint64_t* out, int reset);
 
 /* Number of kernels this library has launched in the process so far. */
 uint64_t bt_launch_count(void);

@@ -42,7 +42,7 @@ class bt_opts(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("modulus", ctypes.c_uint64),
                 ("level_sizes", ctypes.c_void_p), ("nlevels", ctypes.c_uint32),
                 ("max_rounds", ctypes.c_uint64), ("flags", ctypes.c_uint32),
-                ("batch_ctas", ctypes.c_uint32)]
+                ("batch_ctas", ctypes.c_uint32), ("partitions", ctypes.c_uint32)]
 
 
 _lib = None
@@ -94,6 +94,7 @@ def lib() -> ctypes.CDLL:
     L.bt_test_alloc_limit.argtypes = [u64]
     L.bt_test_alloc_limit.restype = None
     L.bt_device_pool_used.argtypes = [P(u64)]
+    L.bt_device_pool_peak.argtypes = [P(u64), ctypes.c_int]
     L.bt_batch_cycles.argtypes = [vp, vp, u32]
     for name in ("bt_profile_read", "bt_build", "bt_build_ex", "bt_build_batch", "bt_access", "bt_rank", "bt_select",
                  "bt_query_batch", "bt_export", "bt_stats", "bt_prefix_fingerprints",
@@ -203,6 +204,13 @@ def bt_batch_cycles(t: int) -> list[int]:
 def bt_test_alloc_limit(nbytes: int) -> None:
     """Test hook: device allocations of a build larger than nbytes fail (0: off)."""
     lib().bt_test_alloc_limit(nbytes)
+
+
+def bt_device_pool_peak(reset: bool = False) -> int:
+    """High-water mark of the stream-ordered pool's bytes (reset: restart it)."""
+    v = ctypes.c_uint64()
+    _check(lib().bt_device_pool_peak(ctypes.byref(v), int(reset)), "bt_device_pool_peak")
+    return v.value
 
 
 def bt_device_pool_used() -> int:
@@ -337,6 +345,7 @@ class BuildOptions:
     batch_ctas: int = 0  # bt_build_batch: CTAs of the batched kernel's launch (0: every SM)
     leaf_counts: bool = False  # no stored counters on the last level (space-efficient rank/select)
     sort_scan: bool = False  # leftmost windows by radix-sorting (fingerprint, position) tuples
+    partitions: int = 0  # with sort_scan: parts of the domain decomposition (0 or 1: one)
 
     def to_c(self):
         o = bt_opts_default()
@@ -346,6 +355,7 @@ class BuildOptions:
         o.modulus = self.modulus
         o.max_rounds = self.max_rounds
         o.batch_ctas = self.batch_ctas
+        o.partitions = self.partitions
         o.flags = ((BT_FLAG_DENSE_SCAN if self.dense_scan else 0)
                    | (BT_FLAG_TINY_QUEUE if self.tiny_queue else 0)
                    | (BT_FLAG_GRAM_LIST if self.gram_list else 0)

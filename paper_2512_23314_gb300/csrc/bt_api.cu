@@ -232,6 +232,7 @@ static int build(const uint8_t* text, uint64_t n, uint32_t sigma, uint32_t tau, 
   ctx.two_phase = (o.flags & BT_FLAG_TWO_PHASE) ? 1 : 0;
   ctx.leaf_counts = (o.flags & BT_FLAG_LEAF_COUNTS) ? 1 : 0;
   ctx.sort_scan = (o.flags & BT_FLAG_SORT_SCAN) ? 1 : 0;
+  ctx.partitions = o.partitions;
   BT_TRY(sc.alloc(&ctx.st, 1));
   BT_CUDA(cudaMemsetAsync(ctx.st, 0, sizeof(Status), s));
   BT_CUDA(cudaMallocHost(&ctx.st_host, sizeof(Status)));
@@ -653,6 +654,22 @@ int bt_device_pool_used(uint64_t* out) {
   uint64_t used = 0;
   BT_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
   *out = used;
+  return BT_OK;
+}
+
+int bt_device_pool_peak(uint64_t* out, int reset) {
+  if (!out) return BT_EINVAL;
+  int dev = 0;
+  BT_CUDA(cudaGetDevice(&dev));
+  cudaMemPool_t pool;
+  BT_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t high = 0;
+  BT_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high));
+  *out = high;
+  if (reset) {
+    uint64_t zero = 0;  // resets the high-water mark to the bytes in use now
+    BT_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+  }
   return BT_OK;
 }
 

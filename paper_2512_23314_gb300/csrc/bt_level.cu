@@ -370,6 +370,93 @@ __global__ void __launch_bounds__(256) k_sort_tail(M m, Geo g, uint32_t bshift, 
 }
 
 // ---------------------------------------------------------------------------
+// 3'''. Domain decomposition of the sort-based pass (section 4.2): the
+// windows of a level are taken in K parts of consecutive windows.  In each
+// part only the windows whose fingerprint is a key's pass the filter (a bit
+// map of the keys' fingerprints, then a binary search in their sorted list),
+// those are sorted, and the first of each fingerprint -- the part's leftmost
+// occurrence -- is kept.  The kept tuples of all parts, at most K per key, are
+// sorted once more; as the parts are in text order and the sort is stable,
+// the first tuple of a key's group is again its leftmost window.  The working
+// memory is a part's tuples plus K tuples per key instead of a tuple per
+// window.
+// ---------------------------------------------------------------------------
+
+// Fingerprints of the keys of one length: a block's (pair = 0) or a pair's
+// (pair = 1), kNone where block k has no such key; each key's bit is set in
+// kbits.
+template <class M>
+__global__ void k_key_list(M m, Geo g, int pair, const uint64_t* __restrict__ fpB,
+                           const uint32_t* __restrict__ slotB, const uint32_t* __restrict__ slotP,
+                           uint64_t* __restrict__ out, uint32_t* __restrict__ kbits, uint64_t kbmask) {
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < g.c;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t F = kNone;
+    if (!pair) {
+      if (slotB[k] != kNoSlot) F = fpB[k];
+    } else if (k + 1 < g.c && slotP[k] != kNoSlot && slotP[k] != kTailPair) {
+      F = m.add(m.mul(fpB[k], g.Bb), fpB[k + 1]);
+    }
+    out[k] = F;
+    if (F != kNone) {
+      const uint64_t bit = mix64(F) & kbmask;
+      atomicOr(&kbits[bit >> 5], 1u << (bit & 31));
+    }
+  }
+}
+
+// Windows [w0, w0 + nw) of length L: the tuple of each, and flag = 1 where
+// its fingerprint is a key's.
+template <class M>
+__global__ void k_part_windows(M m, Geo g, uint64_t L, uint64_t BL, uint32_t bshift, uint64_t w0, uint64_t nw,
+                               const uint32_t* __restrict__ kbits, uint64_t kbmask,
+                               const uint64_t* __restrict__ skeys, uint64_t nk, uint64_t* __restrict__ keys,
+                               uint32_t* __restrict__ vals, uint32_t* __restrict__ flag) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nw;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t w = w0 + i;
+    const uint64_t k = bshift != 0xFFu ? w >> bshift : w / g.b, j = w - k * g.b;
+    const uint64_t p = g.st[k] + j;
+    uint64_t key = kNone;
+    uint32_t f = 0;
+    if (j < blen(g, k) && p + L <= avail_end(g, k)) {
+      key = window_fast(m, g.H, BL, p, L);
+      const uint64_t bit = mix64(key) & kbmask;
+      if ((kbits[bit >> 5] >> (bit & 31)) & 1u) {
+        const uint64_t h = lower_bound_u64(skeys, nk, key);
+        f = h < nk && skeys[h] == key;
+      }
+    }
+    keys[i] = key;
+    vals[i] = (uint32_t)p;
+    flag[i] = f;
+  }
+}
+
+// The tuples i < n with flag[i] = 1 to out[offs[i]] (offs: exclusive prefix
+// sums of flag); *count = their number.
+__global__ void k_compact_tuples(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                                 const uint32_t* __restrict__ flag, const uint32_t* __restrict__ offs, uint64_t n,
+                                 uint64_t* __restrict__ okeys, uint32_t* __restrict__ ovals,
+                                 unsigned long long* count) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    if (flag[i]) {
+      okeys[offs[i]] = keys[i];
+      ovals[offs[i]] = vals[i];
+    }
+    if (i + 1 == n) *count = (unsigned long long)offs[i] + flag[i];
+  }
+}
+
+// flag[i] = 1 for the first tuple of each fingerprint of a sorted list.
+__global__ void k_first_of_key(const uint64_t* __restrict__ keys, uint64_t n, uint32_t* __restrict__ flag) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    flag[i] = i == 0 || keys[i] != keys[i - 1];
+}
+
+// ---------------------------------------------------------------------------
 // 3'. The anchored window scan.
 //
 // Probing the table at every window position costs a random memory access
@@ -1973,28 +2060,143 @@ int exact_pass(const M& m, const Geo& g, uint64_t cpb, int pair, LevelWork& W, c
 
 // The sort-based pass of a level: sorted windows of length b give the block
 // minima, sorted windows of length 2b the pair minima, a dense pass the two
-// tail keys.
+// tail keys.  With parts > 1 the windows are taken in that many parts
+// (domain decomposition, above).
 template <class M>
-int sort_minima(const M& m, const Geo& g, LevelWork& W, uint64_t c, uint64_t b, uint64_t r, cudaStream_t s) {
+int sort_minima(const M& m, const Geo& g, LevelWork& W, uint64_t c, uint64_t b, uint64_t r, uint32_t parts,
+                cudaStream_t s) {
   const uint64_t npos = c * b;
-  if (npos >= (1ull << 32)) return BT_EINVAL;
   const uint32_t bshift = (b & (b - 1)) == 0 ? (uint32_t)__builtin_ctzll(b) : 0xFFu;
-  Scratch sc(s);
-  uint64_t *keys, *tk;
-  uint32_t *vals, *tv, *scr;
-  BT_TRY(sc.alloc(&keys, npos));
-  BT_TRY(sc.alloc(&tk, npos));
-  BT_TRY(sc.alloc(&vals, npos));
-  BT_TRY(sc.alloc(&tv, npos));
-  BT_TRY(sc.alloc(&scr, radix_sort_scratch_words(npos)));
   const unsigned T = 256;
-  for (int pair = 0; pair < 2; pair++) {
-    const uint64_t L = pair ? 2 * b : b;
-    const uint64_t BL = pair ? m.mul(g.Bb, g.Bb) : g.Bb;
-    BT_LAUNCH(k_sort_windows<M><<<grid_for(npos, T), T, 0, s>>>(m, g, L, BL, bshift, keys, vals));
-    BT_TRY(radix_sort_u64_u32(keys, vals, tk, tv, npos, 64, scr, s));
-    BT_LAUNCH(k_sort_minima<M><<<grid_for(c, T), T, 0, s>>>(m, g, pair, W.fpB, W.slotB, W.slotP, W.bt, W.pt, keys,
-                                                            vals, npos));
+  Scratch sc(s);
+  if (parts <= 1) {
+    if (npos >= (1ull << 32)) return BT_EINVAL;
+    uint64_t *keys, *tk;
+    uint32_t *vals, *tv, *scr;
+    BT_TRY(sc.alloc(&keys, npos));
+    BT_TRY(sc.alloc(&tk, npos));
+    BT_TRY(sc.alloc(&vals, npos));
+    BT_TRY(sc.alloc(&tv, npos));
+    BT_TRY(sc.alloc(&scr, radix_sort_scratch_words(npos)));
+    for (int pair = 0; pair < 2; pair++) {
+      const uint64_t L = pair ? 2 * b : b;
+      const uint64_t BL = pair ? m.mul(g.Bb, g.Bb) : g.Bb;
+      BT_LAUNCH(k_sort_windows<M><<<grid_for(npos, T), T, 0, s>>>(m, g, L, BL, bshift, keys, vals));
+      BT_TRY(radix_sort_u64_u32(keys, vals, tk, tv, npos, 64, scr, s));
+      BT_LAUNCH(k_sort_minima<M><<<grid_for(c, T), T, 0, s>>>(m, g, pair, W.fpB, W.slotB, W.slotP, W.bt, W.pt,
+                                                              keys, vals, npos));
+    }
+  } else {
+    if (g.n >= (1ull << 32)) return BT_EINVAL;
+    const uint64_t part = (npos + parts - 1) / parts;  // windows per part
+    uint64_t kbits_n = 4096;
+    while (kbits_n < 32 * c) kbits_n <<= 1;
+    const uint64_t big = std::max<uint64_t>(part, c);
+    uint64_t *skeys, *keys, *ck, *tk;
+    uint32_t *sv, *vals, *cv, *tv, *flag, *offs, *scr, *sagg, *kbits;
+    unsigned long long* d_count;
+    BT_TRY(sc.alloc(&skeys, c));
+    BT_TRY(sc.alloc(&sv, c));
+    BT_TRY(sc.alloc(&kbits, kbits_n / 32));
+    BT_TRY(sc.alloc(&keys, part));
+    BT_TRY(sc.alloc(&vals, part));
+    BT_TRY(sc.alloc(&flag, part));
+    BT_TRY(sc.alloc(&offs, part + 1));  // the scan also writes the total at [n]
+    BT_TRY(sc.alloc(&ck, part));
+    BT_TRY(sc.alloc(&cv, part));
+    BT_TRY(sc.alloc(&tk, big));
+    BT_TRY(sc.alloc(&tv, big));
+    BT_TRY(sc.alloc(&scr, radix_sort_scratch_words(big)));
+    BT_TRY(sc.alloc(&sagg, scan_scratch_words(part)));
+    BT_TRY(sc.alloc(&d_count, 1));
+    // The kept tuples: a list that grows by doubling (at most one tuple per
+    // key fingerprint and part), so that it holds what the parts keep.
+    struct Grown {
+      cudaStream_t s;
+      void* p = nullptr;
+      ~Grown() {
+        if (p) cudaFreeAsync(p, s);
+      }
+    };
+    Grown gk{s}, gv{s};
+    uint64_t kcap = 0;
+    auto reserve_kept = [&](uint64_t need, uint64_t kept) -> int {
+      if (need <= kcap) return BT_OK;
+      const uint64_t cap = std::max<uint64_t>(need, 2 * kcap);
+      void *nk = nullptr, *nv = nullptr;
+      if (!alloc_allowed(cap * sizeof(uint64_t))) return BT_ENOMEM;
+      cudaError_t e1 = cudaMallocAsync(&nk, cap * sizeof(uint64_t), s);
+      cudaError_t e2 = e1 == cudaSuccess ? cudaMallocAsync(&nv, cap * sizeof(uint32_t), s) : e1;
+      if (e2 != cudaSuccess) {
+        if (nk) cudaFreeAsync(nk, s);
+        cudaGetLastError();
+        return e2 == cudaErrorMemoryAllocation ? BT_ENOMEM : BT_ECUDA;
+      }
+      if (kept) {
+        BT_CUDA(cudaMemcpyAsync(nk, gk.p, kept * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        BT_CUDA(cudaMemcpyAsync(nv, gv.p, kept * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+      }
+      if (gk.p) cudaFreeAsync(gk.p, s);
+      if (gv.p) cudaFreeAsync(gv.p, s);
+      gk.p = nk;
+      gv.p = nv;
+      kcap = cap;
+      return BT_OK;
+    };
+    unsigned long long h_count = 0;
+    auto read_count = [&](uint64_t* out) -> int {
+      BT_CUDA(cudaMemcpyAsync(&h_count, d_count, sizeof(h_count), cudaMemcpyDeviceToHost, s));
+      BT_CUDA(cudaStreamSynchronize(s));
+      *out = h_count;
+      return BT_OK;
+    };
+    for (int pair = 0; pair < 2; pair++) {
+      const uint64_t L = pair ? 2 * b : b;
+      const uint64_t BL = pair ? m.mul(g.Bb, g.Bb) : g.Bb;
+      // The keys of this length: a bit map and the sorted list.
+      BT_CUDA(cudaMemsetAsync(kbits, 0, kbits_n / 8, s));
+      BT_LAUNCH(k_key_list<M><<<grid_for(c, T), T, 0, s>>>(m, g, pair, W.fpB, W.slotB, W.slotP, skeys, kbits,
+                                                           kbits_n - 1));
+      BT_TRY(radix_sort_u64_u32(skeys, sv, tk, tv, c, 64, scr, s));
+      uint64_t kept = 0;
+      for (uint64_t w0 = 0; w0 < npos; w0 += part) {
+        const uint64_t nw = std::min(part, npos - w0);
+        BT_LAUNCH(k_part_windows<M><<<grid_for(nw, T), T, 0, s>>>(m, g, L, BL, bshift, w0, nw, kbits, kbits_n - 1,
+                                                                  skeys, c, keys, vals, flag));
+        BT_TRY(scan_u32(flag, offs, nw, s, sagg));
+        BT_LAUNCH(k_compact_tuples<<<grid_for(nw, T), T, 0, s>>>(keys, vals, flag, offs, nw, ck, cv, d_count));
+        uint64_t nm = 0;
+        BT_TRY(read_count(&nm));
+        if (nm == 0) continue;
+        BT_TRY(radix_sort_u64_u32(ck, cv, tk, tv, nm, 64, scr, s));
+        BT_LAUNCH(k_first_of_key<<<grid_for(nm, T), T, 0, s>>>(ck, nm, flag));
+        BT_TRY(scan_u32(flag, offs, nm, s, sagg));
+        // The part keeps at most one tuple per key fingerprint.
+        BT_TRY(reserve_kept(kept + std::min<uint64_t>(nm, c), kept));
+        BT_LAUNCH(k_compact_tuples<<<grid_for(nm, T), T, 0, s>>>(ck, cv, flag, offs, nm, (uint64_t*)gk.p + kept,
+                                                                 (uint32_t*)gv.p + kept, d_count));
+        uint64_t nu = 0;
+        BT_TRY(read_count(&nu));
+        kept += nu;
+      }
+      if (kept) {
+        uint64_t* kk = (uint64_t*)gk.p;
+        uint32_t* kv = (uint32_t*)gv.p;
+        if (kept <= big) {
+          BT_TRY(radix_sort_u64_u32(kk, kv, tk, tv, kept, 64, scr, s));
+        } else {
+          Scratch sc2(s);
+          uint64_t* tkk;
+          uint32_t *tkv, *scr2;
+          BT_TRY(sc2.alloc(&tkk, kept));
+          BT_TRY(sc2.alloc(&tkv, kept));
+          BT_TRY(sc2.alloc(&scr2, radix_sort_scratch_words(kept)));
+          BT_TRY(radix_sort_u64_u32(kk, kv, tkk, tkv, kept, 64, scr2, s));
+        }
+        BT_LAUNCH(k_sort_minima<M><<<grid_for(c, T), T, 0, s>>>(m, g, pair, W.fpB, W.slotB, W.slotP, W.bt, W.pt,
+                                                                kk, kv, kept));
+      }
+    }
   }
   if (r) BT_LAUNCH(k_sort_tail<M><<<grid_for(npos, T), T, 0, s>>>(m, g, bshift, W.fpB, W.slotP, W.ld));
   BT_CUDA(cudaGetLastError());
@@ -2131,7 +2333,7 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
                                            ctx.st));
   if (ctx.sort_scan) {
     ProfScope ps("window_scan", s, cov_l);
-    BT_TRY(sort_minima(m, g, W, c, b, r, s));
+    BT_TRY(sort_minima(m, g, W, c, b, r, ctx.partitions, s));
   } else if (!anchored) {
     ProfScope ps("window_scan", s, cov_l);
     BT_LAUNCH(k_scan<M><<<grid_for(c * cpb, T), T, 0, s>>>(m, g, cpb, W.bt, bcap - 1, W.pt, pcap - 1,
