@@ -21,7 +21,8 @@ answers a batch of mixed access / rank / select queries on its resident tree
 Reported: p50 / p99 build latency (arrival -> tree ready) and query-batch
 latency, admission wait (arrival -> build start), offered and sustained
 documents per second, the largest backlog of waiting documents, the number
-of micro-batches and their mean size.
+of micro-batches and their mean size, and the lanes' summed seconds in large
+builds, micro-batches and queries.
 """
 from __future__ import annotations
 
@@ -77,6 +78,7 @@ class Report:
     large_docs: int
     max_concurrent: int
     evictions: int
+    lane_seconds: dict = field(default_factory=dict)  # summed over lanes: large builds, batches, queries
     results: list = field(default_factory=list, repr=False)
 
     def summary(self) -> dict:
@@ -87,7 +89,7 @@ class Report:
 
 class Server:
     def __init__(self, hbm_budget: int = 120 << 30, lanes: int = 4, queries_per_doc: int = 10_000,
-                 small_max: int = 4 << 20, max_batch_docs: int = 512, keep_exports: bool = False,
+                 small_max: int = 1 << 20, max_batch_docs: int = 512, keep_exports: bool = False,
                  keep_queries: int = 0, seed: int = 0, sm_count: int | None = None):
         self.budget = hbm_budget
         self.lanes = lanes
@@ -154,43 +156,51 @@ class Server:
             self._lock.notify_all()
 
     # -- queries -----------------------------------------------------------
-    def _queries(self, handle: int, n: int, rng: np.random.Generator, stream,
-                 keep: int = 0) -> tuple[float, dict | None]:
-        """One batch of mixed queries on a resident tree, all on `stream` (the
-        argument tensors are made inside the stream context, so no kernel of
-        another stream writes them).  With keep > 0 the first `keep`
+    def _queries(self, handle: int, n: int, rng, stream, keep: int = 0) -> tuple[float, dict | None]:
+        """One batch of mixed queries on a resident tree, all on `stream`:
+        the symbol counts (rank at n), then access / rank / select arguments
+        drawn on the device from the lane's generator `rng` (symbols among
+        those present, select ranks within their counts), the three query
+        launches and one synchronisation.  With keep > 0 the first `keep`
         arguments and answers of each kind are returned for checking."""
         t0 = time.perf_counter()
+        q = self.qpd // 3
         with torch.cuda.stream(stream):
-            syms = torch.arange(256, dtype=torch.int64, device="cuda")
+            dev = torch.device("cuda")
+            syms = torch.arange(256, dtype=torch.int64, device=dev)
             cnt_args = torch.stack([syms, torch.full_like(syms, n)], 1).reshape(-1).contiguous()
-            counts = torch.empty(256, dtype=torch.int64, device="cuda")
+            counts = torch.empty(256, dtype=torch.int64, device=dev)
             bt.bt_query_batch(handle, bt.BT_Q_RANK, cnt_args, 256, counts, stream)
-            c = counts.cpu().numpy()
-            present = np.flatnonzero(c > 0)
-            q = self.qpd // 3
-            acc_h = rng.integers(0, n, q)
-            cs = rng.choice(present, q)
-            rk_h = np.stack([cs, rng.integers(0, n + 1, q)], 1).reshape(-1)
-            cs2 = rng.choice(present, q)
-            js = (rng.random(q) * c[cs2]).astype(np.int64) + 1
-            sl_h = np.stack([cs2, js], 1).reshape(-1)
-            acc = torch.from_numpy(acc_h).to("cuda", non_blocking=True)
-            rk = torch.from_numpy(rk_h).cuda()
-            sl = torch.from_numpy(sl_h).cuda()
-            out = torch.empty(3 * q, dtype=torch.int64, device="cuda")
+            # The present symbols first, in byte order; np_ of them.
+            present = torch.sort((counts == 0).to(torch.int8), stable=True).indices
+            np_ = (counts > 0).sum()
+
+            def pick():
+                u = torch.randint(0, 1 << 30, (q,), generator=rng, device=dev)
+                return present[u % np_]
+
+            acc = torch.randint(0, n, (q,), generator=rng, device=dev)
+            cs = pick()
+            rk = torch.stack([cs, torch.randint(0, n + 1, (q,), generator=rng, device=dev)], 1).reshape(-1)
+            cs2 = pick()
+            cnt2 = counts[cs2]
+            js = torch.minimum((torch.rand(q, generator=rng, device=dev, dtype=torch.float64) * cnt2)
+                               .to(torch.int64) + 1, cnt2)
+            sl = torch.stack([cs2, js], 1).reshape(-1)
+            rk, sl = rk.contiguous(), sl.contiguous()
+            out = torch.empty(3 * q, dtype=torch.int64, device=dev)
             bt.bt_query_batch(handle, bt.BT_Q_ACCESS, acc, q, out[:q], stream)
             bt.bt_query_batch(handle, bt.BT_Q_RANK, rk, q, out[q:2 * q], stream)
             bt.bt_query_batch(handle, bt.BT_Q_SELECT, sl, q, out[2 * q:], stream)
-            res = out.cpu().numpy()
-        dt = time.perf_counter() - t0
-        kept = None
-        if keep:
-            k = min(keep, q)
-            kept = {"access": (acc_h[:k].copy(), res[:k].copy()),
-                    "rank": (rk_h[:2 * k].reshape(-1, 2).copy(), res[q:q + k].copy()),
-                    "select": (sl_h[:2 * k].reshape(-1, 2).copy(), res[2 * q:2 * q + k].copy())}
-        return dt, kept
+            kept = None
+            if keep:
+                k = min(keep, q)
+                res = out.cpu().numpy()
+                kept = {"access": (acc[:k].cpu().numpy(), res[:k].copy()),
+                        "rank": (rk[:2 * k].reshape(-1, 2).cpu().numpy(), res[q:q + k].copy()),
+                        "select": (sl[:2 * k].reshape(-1, 2).cpu().numpy(), res[2 * q:2 * q + k].copy())}
+            stream.synchronize()
+        return time.perf_counter() - t0, kept
 
     # -- main loop ---------------------------------------------------------
     def run(self, arrivals: list[Arrival]) -> Report:
@@ -203,6 +213,7 @@ class Server:
         finished = [0]
         errors = []
         stats = {"backlog": 0, "batches": 0, "batch_docs": 0, "large": 0}
+        lane_s = {"large_build": 0.0, "batch_build": 0.0, "queries": 0.0}
         if self.sm_count is None:
             try:
                 self.sm_count = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
@@ -228,9 +239,15 @@ class Server:
                 if results[first].n > self.small_max:
                     pending.popleft()
                     return [first]
-                batch = []
-                while pending and len(batch) < self.max_batch_docs and results[pending[0]].n <= self.small_max:
-                    batch.append(pending.popleft())
+                # The small documents waiting, in arrival order, up to a batch;
+                # the large ones among them keep their places.
+                batch, rest = [], collections.deque()
+                while pending and len(batch) < self.max_batch_docs:
+                    i = pending.popleft()
+                    (batch if results[i].n <= self.small_max else rest).append(i)
+                rest.extend(pending)
+                pending.clear()
+                pending.extend(rest)
                 return batch
 
         def serve_unit(unit, stream, rng):
@@ -271,6 +288,8 @@ class Server:
                         stats["batches"] += 1
                         stats["batch_docs"] += len(unit)
                 t1 = time.perf_counter() - t_start
+                with qlock:
+                    lane_s["large_build" if results[unit[0]].n > self.small_max else "batch_build"] += t1 - t0
                 for i, h in zip(unit, handles):
                     r = results[i]
                     r.built = t1
@@ -278,6 +297,8 @@ class Server:
                         r.export = bt.bt_export(h)
                     r.query_batch_s, r.queries = self._queries(h, r.n, rng, stream, self.keep_queries)
                     r.queried = time.perf_counter() - t_start
+                with qlock:
+                    lane_s["queries"] += time.perf_counter() - t_start - t1
             except BaseException:
                 for h in handles:
                     if h is not None:
@@ -290,8 +311,17 @@ class Server:
             return len(unit)
 
         def lane(widx: int):
-            stream = torch.cuda.Stream()
-            rng = np.random.default_rng(self.seed * 1000 + widx)
+            try:
+                stream = torch.cuda.Stream()
+                rng = None  # without a device (host tests) the queries take no generator
+                if torch.cuda.is_available():
+                    rng = torch.Generator(device="cuda")
+                    rng.manual_seed(self.seed * 1000 + widx)
+            except BaseException as e:  # a lane that cannot start: recorded like a failed unit
+                with qlock:
+                    errors.append(e)
+                    qlock.notify_all()
+                return
             while True:
                 unit = take()
                 if unit is None:
@@ -318,7 +348,7 @@ class Server:
         if n_total == 0:
             done.set()
         with qlock:
-            while not done.is_set() and not (errors and not any(th.is_alive() for th in threads)):
+            while not done.is_set() and any(th.is_alive() for th in threads):
                 qlock.wait(timeout=1.0)
             done.set()
             qlock.notify_all()
@@ -326,6 +356,8 @@ class Server:
             th.join()
         wall = time.perf_counter() - t_start
         torch.cuda.synchronize()
+        if not errors and finished[0] < n_total:
+            raise RuntimeError(f"serving lanes ended with {n_total - finished[0]} documents unserved")
         if errors:
             raise errors[0]
         build_lat = np.array([r.built - r.arrival for r in results]) * 1e3
@@ -343,7 +375,7 @@ class Server:
             queries_per_doc=3 * (self.qpd // 3), max_backlog=stats["backlog"], batches=stats["batches"],
             mean_batch_docs=stats["batch_docs"] / stats["batches"] if stats["batches"] else 0.0,
             large_docs=stats["large"], max_concurrent=self._max_inflight, evictions=self._evictions,
-            results=results)
+            lane_seconds=lane_s, results=results)
 
     def close(self):
         with self._lock:

@@ -139,3 +139,49 @@ def test_small_documents_go_out_in_micro_batches(fake_lib, monkeypatch):
     with pytest.raises(RuntimeError, match="batch failed"):
         s2.run(_arrivals(10))
     assert s2._inflight == 0 and s2._charged == 0
+
+
+def test_lane_that_cannot_start_ends_run(fake_lib, monkeypatch):
+    """A lane whose stream cannot be made is recorded like a failed unit:
+    run() raises that error instead of waiting for documents nobody serves."""
+    def no_stream():
+        raise RuntimeError("no stream")
+
+    monkeypatch.setattr(serve.torch.cuda, "Stream", no_stream)
+    monkeypatch.setattr(serve.torch.cuda, "synchronize", lambda *a: None)
+    s = serve.Server(hbm_budget=1 << 40, lanes=2, small_max=0)
+    t0 = time.perf_counter()
+    with pytest.raises(RuntimeError, match="no stream"):
+        s.run(_arrivals(4))
+    assert time.perf_counter() - t0 < 10
+
+
+def test_small_documents_behind_a_large_one_share_a_batch(fake_lib, monkeypatch):
+    """Small documents waiting behind large ones are gathered into one
+    micro-batch; the large ones keep their places and are built alone."""
+    monkeypatch.setattr(serve.torch.cuda, "Stream", _FakeStream)
+    monkeypatch.setattr(serve.torch.cuda, "synchronize", lambda *a: None)
+    monkeypatch.setattr(serve.bt, "bt_opts_default", lambda: serve.bt.bt_opts())
+    batches, alone = [], []
+
+    def fake_batch(texts, ns, sigmas, taus, leafs, opts, nworkers=0):
+        batches.append(list(ns))
+        return [f"b{n}" for n in ns]
+
+    def fake_build(text, n, sigma, tau, leaf, opts, stream):
+        alone.append(n)
+        return f"h{n}"
+
+    monkeypatch.setattr(serve.bt, "bt_build_batch", fake_batch)
+    monkeypatch.setattr(serve.bt, "bt_build_ex", fake_build)
+    monkeypatch.setattr(serve.Server, "_queries", lambda self, h, n, rng, stream, keep=0: (0.0, None))
+    from paper_2512_23314_gb300.workloads import Arrival, Doc
+    import numpy as np
+    sizes = [64, 2000, 65, 66, 2001, 67, 68]  # two large (> small_max = 1000) among small ones
+    arr = [Arrival(0.0, Doc(np.zeros(k, np.uint8), 4, 2, 16)) for k in sizes]
+    s = serve.Server(hbm_budget=1 << 40, lanes=1, small_max=1000, sm_count=152)
+    rep = s.run(arr)
+    assert rep.docs == len(sizes)
+    assert sorted(alone) == [2000, 2001]
+    assert sorted(n for b in batches for n in b) == [64, 65, 66, 67, 68]
+    assert len(batches) <= 2
