@@ -85,7 +85,11 @@ def parse_args():
     ap.add_argument("--summarize-launches", metavar="CSV",
                     help="summarize an ncu launch list (--metrics gpu__time_duration.sum --csv) and exit")
     ap.add_argument("--builds", type=int, default=1,
-                    help="builds the launch list covers (with --summarize-launches)")
+                    help="builds the launch list covers (with --summarize-launches / --summarize-traffic)")
+    ap.add_argument("--summarize-traffic", nargs=3, metavar=("CSV", "BENCH_JSON", "OUT_JSON"),
+                    help="window-scan DRAM traffic from an ncu capture (--metrics dram__bytes_read.sum,"
+                         "dram__bytes_write.sum,gpu__time_duration.sum --csv) of the same build as the "
+                         "bench line in BENCH_JSON; writes the traffic record and exits")
     return ap.parse_args()
 
 
@@ -117,6 +121,60 @@ def summarize_launches(path: str, builds: int) -> None:
             n = len(per[k]) // builds
             lo = n if builds > 1 else 0
             print(k, "per level:", " ".join(f"{x:.3f}" for x in per[k][lo:lo + n]))
+
+
+SCAN_KERNELS = ("k_scan", "k_hits", "k_candidates<")
+TRAFFIC_CMD = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+               "--clock-control none -k \"regex:k_scan|k_hits|k_candidates\" --csv --log-file dram.csv "
+               "python bench.py --workload text_versions_160MiB --steps 1 --warmup 0 --no-cpu-baseline --no-extras")
+
+
+def summarize_traffic(csv_path: str, bench_json: str, out_path: str, builds: int) -> None:
+    """DRAM bytes of the window-scan kernels per build, from an ncu capture
+    of `builds` identical builds, against the algorithmic bytes (the summed
+    level coverage) of the bench line of the same workload; written as the
+    traffic record that roofline.traffic reads (keyed by the scan source's
+    hash).  The prune pass's own candidate kernel (`k_candidates` without a
+    template argument) is not part of the window scan."""
+    import collections
+    import csv
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "nsecond": 1e-6, "usecond": 1e-3,
+             "msecond": 1.0, "second": 1e3, "ns": 1e-6, "us": 1e-3, "ms": 1.0, "s": 1e3}
+    rows = [r for r in csv.reader(open(csv_path)) if len(r) > 10]
+    hdr, rows = rows[0], rows[1:]
+    i_name, i_metric = hdr.index("Kernel Name"), hdr.index("Metric Name")
+    i_unit, i_val = hdr.index("Metric Unit"), hdr.index("Metric Value")
+    agg = collections.defaultdict(lambda: {"ids": set(), "dram_read_bytes": 0.0, "dram_write_bytes": 0.0,
+                                           "ms": 0.0})
+    i_id = hdr.index("ID")
+    for r in rows:
+        name = r[i_name].split("(")[0].replace("void ", "").replace("(anonymous namespace)::", "")
+        name = name.replace("unnamed>::", "").strip()
+        if not any(name.startswith(k) for k in SCAN_KERNELS):
+            continue
+        v = float(r[i_val].replace(",", "")) * scale.get(r[i_unit], 1.0)
+        a = agg[name]
+        a["ids"].add(r[i_id])
+        key = {"dram__bytes_read.sum": "dram_read_bytes", "dram__bytes_write.sum": "dram_write_bytes",
+               "gpu__time_duration.sum": "ms"}.get(r[i_metric])
+        if key:
+            a[key] += v
+    line = json.loads(open(bench_json).read().strip().splitlines()[-1])
+    alg = line["config"]["sum_cov_bytes"]
+    per = {k: {"launches_per_build": len(a["ids"]) // builds,
+               "dram_read_bytes": int(a["dram_read_bytes"] / builds),
+               "dram_write_bytes": int(a["dram_write_bytes"] / builds),
+               "ms": round(a["ms"] / builds, 4)} for k, a in agg.items()}
+    dram = sum(p["dram_read_bytes"] + p["dram_write_bytes"] for p in per.values())
+    rec = {"kernel": "window_scan", "source": os.path.relpath(SCAN_SOURCE, ROOT),
+           "source_sha256_16": source_hash(SCAN_SOURCE),
+           "workload": f"{line['config']['workload']} (n = {line['config']['n']}, tau {line['config']['tau']}, "
+                       f"leaf {line['config']['leaf_len']}, prune on), {line['config']['levels']} levels",
+           "command": TRAFFIC_CMD, "builds_captured": builds, "alg_bytes_per_build": alg, "dram_bytes_per_build": dram,
+           "dram_bytes_per_alg_byte": round(dram / alg, 4), "per_kernel": per}
+    with open(out_path, "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps(rec, indent=1))
 
 
 def measured_peaks() -> dict:
@@ -755,6 +813,8 @@ def main():
     args = parse_args()
     if args.summarize_launches:
         summarize_launches(args.summarize_launches, args.builds)
+    elif args.summarize_traffic:
+        summarize_traffic(*args.summarize_traffic, args.builds)
     elif args.batch_only:
         import torch
         torch.cuda.set_device(0)

@@ -125,6 +125,9 @@ __device__ __forceinline__ void fail(Cta& C, int code) { atomicCAS(&C.err, 0, co
 __device__ __forceinline__ void min_pos(unsigned long long* a, uint64_t p) {
   if (*(volatile unsigned long long*)a > p) atomicMin(a, (unsigned long long)p);
 }
+// The same without the read: an atomic whose result is not used (a reduction
+// the thread does not wait for), for the scan's frequent hits.
+__device__ __forceinline__ void red_min(unsigned long long* a, uint64_t p) { atomicMin(a, (unsigned long long)p); }
 
 template <class M>
 __device__ __forceinline__ uint64_t phi(const M& m, const uint64_t* __restrict__ H, uint64_t BL, uint64_t p,
@@ -466,7 +469,7 @@ __device__ __forceinline__ void window_hit(const M& m, const ScanArgs& A, uint64
                                         uint64_t hb) {
   const uint32_t sl = t_find(A.bt, A.bmask, x);
   if (sl == kNoSlot) return;
-  min_pos(&A.bt[sl].lo, p);
+  red_min(&A.bt[sl].lo, p);
   if (A.r && sl == A.pretail && p + A.b + A.r <= av && m.sub(A.H[p + A.b + A.r], m.mul(hb, A.Br)) == A.fp_tail)
     min_pos(A.lo_tailpair, p);
   if (p <= A.bt[sl].maxpst && p + 2 * A.b <= av) {
@@ -474,7 +477,7 @@ __device__ __forceinline__ void window_hit(const M& m, const ScanArgs& A, uint64
     const uint32_t s2 = t_find(A.bt, A.bmask, fp2);
     if (s2 != kNoSlot) {
       const uint32_t ps = t_find(A.pt, A.pmask, ((uint64_t)sl << 32) | s2);
-      if (ps != kNoSlot) min_pos(&A.pt[ps].lo, p);
+      if (ps != kNoSlot) red_min(&A.pt[ps].lo, p);
     }
   }
 }
