@@ -92,6 +92,9 @@ struct Cta {
   unsigned long long fp_tail, lo_tail, lo_tailpair;
   uint32_t pretail;
   unsigned int npairs, njobs, nsusp;
+  uint32_t nsel;                      // selected grams of the document (kNoList: none kept)
+  unsigned int anchorless;            // some key of the level has no selected gram
+  uint32_t tail_g, tail_a, tail_anchored;  // anchor of the short tail key
   unsigned long long verify_bytes, collisions;
   unsigned long long lastk;
   // scans
@@ -378,6 +381,122 @@ __device__ void prefix_pass(const M& m, const uint8_t* __restrict__ T, uint64_t 
 // ---------------------------------------------------------------------------
 // One level.
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Selected grams: the anchors of the window scan on levels with long blocks.
+// A window's anchor is its first 16-byte gram whose hash is selected; a
+// window equal to a key has the key's anchor gram at the key's anchor offset,
+// so on those levels only the selected grams of the level's runs are read and
+// each proposes the windows that would have it as their anchor.  The grams
+// are selected once per document; a level looks them up in the list.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kNoList = 0xFFFFFFFFu;        // the list overflowed: no anchors
+constexpr unsigned long long kNoAnchor = ~0ull;  // empty anchor-table entry
+
+__device__ __forceinline__ uint32_t gram_hash(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3) {
+  uint32_t h = w0 * 0x9E3779B1u;
+  uint32_t t = w1 * 0x85EBCA77u;
+  h ^= __funnelshift_l(t, t, 13);
+  t = w2 * 0xC2B2AE3Du;
+  h ^= __funnelshift_l(t, t, 7);
+  t = w3 * 0x27D4EB2Fu;
+  h ^= __funnelshift_l(t, t, 19);
+  h ^= h >> 16;
+  h *= 0x7FEB352Du;
+  h ^= h >> 15;
+  h *= 0x846CA68Bu;
+  h ^= h >> 16;
+  return h;
+}
+
+__device__ __forceinline__ uint32_t anchor_slot(uint32_t g, uint64_t mask) {
+  return (uint32_t)(((uint64_t)g * 0x9E3779B97F4A7C15ull >> 32) & mask);
+}
+
+// Exclusive sum of one value per thread over the CTA; *total = the sum.
+__device__ uint32_t cta_excl_u32(uint32_t v, Cta& C, uint32_t* total) {
+  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t o = __shfl_up_sync(kFull, x, d);
+    if ((int)lane >= d) x += o;
+  }
+  if (lane == 31) C.wtot[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < nw ? C.wtot[lane] : 0u;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t o = __shfl_up_sync(kFull, w, d);
+      if ((int)lane >= d) w += o;
+    }
+    C.wtot[lane] = w;
+  }
+  __syncthreads();
+  const uint32_t r = (warp ? C.wtot[warp - 1] : 0u) + x - v;
+  *total = C.wtot[nw - 1];
+  __syncthreads();
+  return r;
+}
+
+// The selected grams of T[0, n) in text order: positions and hashes, at most
+// cap of them (C.nsel = their number, or kNoList if there are more).  A
+// thread takes 32 consecutive positions of a tile, from 12 aligned words
+// (the text is followed by at least 48 readable bytes).
+__device__ void gram_list_pass(const uint8_t* __restrict__ T, uint64_t n, uint32_t* __restrict__ lpos,
+                               uint32_t* __restrict__ lhash, uint64_t cap, Cta& C) {
+  if (threadIdx.x == 0) C.nsel = 0;
+  __syncthreads();
+  const uint64_t npos = n >= kGramW ? n - kGramW + 1 : 0;
+  const uint64_t tile = (uint64_t)blockDim.x * 32;
+  for (uint64_t t0 = 0; t0 < npos; t0 += tile) {
+    const uint64_t x0 = t0 + 32ull * threadIdx.x;
+    uint32_t w[12];
+    uint32_t mask = 0;
+    if (x0 < npos) {
+      const uint32_t* wp = (const uint32_t*)(T + x0);
+#pragma unroll
+      for (int k = 0; k < 12; k++) w[k] = wp[k];
+#pragma unroll
+      for (int i = 0; i < 32; i++) {
+        const int q = i >> 2, sh = 8 * (i & 3);
+        const uint32_t h = gram_hash(__funnelshift_r(w[q], w[q + 1], sh), __funnelshift_r(w[q + 1], w[q + 2], sh),
+                                     __funnelshift_r(w[q + 2], w[q + 3], sh), __funnelshift_r(w[q + 3], w[q + 4], sh));
+        if ((h >> kGramSelShift) == 0 && x0 + i < npos) mask |= 1u << i;
+      }
+    }
+    uint32_t total;
+    const uint32_t before = cta_excl_u32(__popc(mask), C, &total);
+    const uint32_t base = C.nsel;
+    if (base != kNoList && (uint64_t)base + total <= cap) {
+      uint32_t o = base + before;
+#pragma unroll
+      for (int i = 0; i < 32; i++) {
+        if (!((mask >> i) & 1u)) continue;
+        const int q = i >> 2, sh = 8 * (i & 3);
+        lpos[o] = (uint32_t)(x0 + i);
+        lhash[o] = gram_hash(__funnelshift_r(w[q], w[q + 1], sh), __funnelshift_r(w[q + 1], w[q + 2], sh),
+                             __funnelshift_r(w[q + 2], w[q + 3], sh), __funnelshift_r(w[q + 3], w[q + 4], sh));
+        o++;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) C.nsel = (base == kNoList || (uint64_t)base + total > cap) ? kNoList : base + total;
+    __syncthreads();
+  }
+}
+
+// First index i of the sorted a[0, n) with a[i] >= x.
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__ a, uint32_t n, uint64_t x) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
 struct Work {
   uint64_t *fpB, *job_of, *susp, *exBL;
   unsigned long long* exlo;
@@ -387,6 +506,7 @@ struct Work {
   BJob* jobs;
   BSlot* bt;
   PSlot* pt;
+  unsigned long long* at;  // anchor table: (gram hash << 32) | anchor offset
 };
 
 __device__ __forceinline__ char* carve(char*& p, uint64_t bytes) {
@@ -412,6 +532,7 @@ __device__ Work carve_level(char* temp, uint64_t c, uint64_t bcap, uint64_t pcap
   carve(p, c * 8 + 8);
   W.bt = (BSlot*)carve(p, bcap * 32);
   W.pt = (PSlot*)carve(p, pcap * 16);
+  W.at = (unsigned long long*)carve(p, bcap * 8);
   return W;
 }
 
@@ -575,20 +696,72 @@ __device__ void level_pass(const M& m, const BParams& P, const BDoc& D, Cta& C, 
     }
   }
   if (cta_failed(C)) return;
+  // Levels of long blocks scan by anchors: every full-length block registers
+  // its first selected gram (hash, offset from the block's start) in the
+  // anchor table, each distinct (hash, offset) once.  Registering every block,
+  // not one per table slot, keeps the proposals complete when different
+  // contents share a fingerprint.  A block without a selected gram sends the
+  // level to the rolling scan below.
+  const uint32_t* lpos = (const uint32_t*)(scr + C.sl.lpos);
+  const uint32_t* lhash = (const uint32_t*)(scr + C.sl.lhash);
+  const uint32_t nsel = C.nsel;
+  const uint64_t amask = bcap - 1;
+  bool anch = b >= kAnchorMinB && nsel != kNoList;
+  if (anch) {
+    if (tid == 0) {
+      C.anchorless = 0;
+      C.tail_anchored = 0;
+      if (r >= kGramW) {
+        const uint64_t ts = C.last_start;
+        const uint32_t j = lower_bound_u32(lpos, nsel, ts);
+        if (j < nsel && lpos[j] + kGramW <= ts + r) {
+          C.tail_g = lhash[j];
+          C.tail_a = (uint32_t)(lpos[j] - ts);
+          C.tail_anchored = 1;
+        }
+      }
+    }
+    for (uint64_t i = tid; i < bcap; i += nt) W.at[i] = kNoAnchor;
+    __syncthreads();
+    for (uint64_t k = tid; k < c; k += nt) {
+      if (W.slotB[k] == kNoSlot) continue;
+      const uint64_t s0 = g.st[k];
+      const uint32_t j = lower_bound_u32(lpos, nsel, s0);
+      if (j >= nsel || lpos[j] + kGramW > s0 + b) {
+        atomicOr(&C.anchorless, 1u);
+        continue;
+      }
+      const unsigned long long e = ((unsigned long long)lhash[j] << 32) | (uint32_t)(lpos[j] - s0);
+      uint32_t h = anchor_slot(lhash[j], amask);
+      for (uint64_t it = 0; it <= amask; it++) {
+        const unsigned long long cur = *(volatile unsigned long long*)&W.at[h];
+        if (cur == e) break;
+        if (cur == kNoAnchor) {
+          const unsigned long long old = atomicCAS(&W.at[h], kNoAnchor, e);
+          if (old == kNoAnchor || old == e) break;
+        }
+        h = (uint32_t)((h + 1) & amask);
+      }
+    }
+    __syncthreads();
+    anch = C.anchorless == 0;
+  }
   // A bitmap of the full-length block fingerprints in shared memory (about
   // 32 bits per key): a window whose fingerprint's bit is clear matches no
   // key, so only the few that pass probe the table in global memory.
   uint32_t fwords = 32;
   while (fwords < c && fwords < filt_words_max) fwords <<= 1;
   const uint64_t fmask = (uint64_t)fwords * 32 - 1;
-  for (uint32_t i = tid; i < fwords; i += nt) filt[i] = 0;
-  for (uint32_t a = tid; a < 256; a += nt) C.rtab[a] = m.mul(a + 1, Bb);
-  __syncthreads();
-  for (uint64_t k = tid; k < c; k += nt)
-    if (W.slotB[k] != kNoSlot) {
-      const uint64_t bit = W.fpB[k] & fmask;
-      atomicOr(&filt[bit >> 5], 1u << (bit & 31));
-    }
+  if (!anch) {
+    for (uint32_t i = tid; i < fwords; i += nt) filt[i] = 0;
+    for (uint32_t a = tid; a < 256; a += nt) C.rtab[a] = m.mul(a + 1, Bb);
+    __syncthreads();
+    for (uint64_t k = tid; k < c; k += nt)
+      if (W.slotB[k] != kNoSlot) {
+        const uint64_t bit = W.fpB[k] & fmask;
+        atomicOr(&filt[bit >> 5], 1u << (bit & 31));
+      }
+  }
   __syncthreads();
   tmark(C, 1);
 
@@ -611,7 +784,73 @@ __device__ void level_pass(const M& m, const BParams& P, const BDoc& D, Cta& C, 
       }
     }
     const ScanArgs A{H, W.bt, W.pt, bmask, pmask, b, r, Bb, Br, fp_tail, pretail, &C.lo_tailpair};
-    if (b % 32 == 0) {
+    if (anch) {
+      // A warp per present block k: its selected grams x (the list entries
+      // in [s_k, s_k + len_k)) propose, for every key anchored on the gram's
+      // hash at offset a, the window at p = x - a.  As a < b, p lies in
+      // block k or in block k-1 when that one ends where k starts; the
+      // window must end within the run of p's block.
+      const unsigned lane = tid & 31, nw = nt >> 5;
+      const bool tail_anch = r && C.tail_anchored;
+      const uint32_t tail_g = C.tail_g, tail_a = C.tail_a;
+      for (uint64_t k = tid >> 5; k < c; k += nw) {
+        const uint64_t s = g.st[k];
+        const uint64_t len = n - s < b ? n - s : b, e0 = s + len;
+        uint64_t av = e0;  // run end of block k
+        uint64_t nxt = 0;  // length of block k+1 when it follows k
+        if (k + 1 < c && g.st[k + 1] == e0) {
+          nxt = n - e0 < b ? n - e0 : b;
+          av = e0 + nxt;
+          if (k + 2 < c && g.st[k + 2] == av) av += n - av < b ? n - av : b;
+        }
+        const bool prev = k > 0 && g.st[k - 1] + b == s;  // block k-1 ends where k starts
+        const uint64_t av_prev = e0 + nxt;                // run end of block k-1
+        uint32_t j0 = 0, j1 = 0;
+        if (lane == 0) {
+          j0 = lower_bound_u32(lpos, nsel, s);
+          j1 = lower_bound_u32(lpos, nsel, e0);
+        }
+        j0 = __shfl_sync(kFull, j0, 0);
+        j1 = __shfl_sync(kFull, j1, 0);
+        for (uint32_t j = j0 + lane; j < j1; j += 32) {
+          const uint64_t x = lpos[j];
+          const uint32_t gh = lhash[j];
+          uint32_t h = anchor_slot(gh, amask);
+          for (uint64_t it = 0; it <= amask; it++) {
+            const unsigned long long en = W.at[h];
+            if (en == kNoAnchor) break;
+            if ((uint32_t)(en >> 32) == gh && (uint32_t)en <= x) {
+              const uint64_t p = x - (uint32_t)en;
+              const uint64_t pav = p >= s ? av : (prev ? av_prev : 0);
+              if (p + b <= pav) {
+                const uint64_t hb = H[p + b];
+                window_hit(m, A, p, pav, m.sub(hb, m.mul(H[p], Bb)), hb);
+              }
+            }
+            h = (uint32_t)((h + 1) & amask);
+          }
+          if (tail_anch && gh == tail_g && tail_a <= x) {
+            const uint64_t p = x - tail_a;
+            const uint64_t pav = p >= s ? av : (prev ? av_prev : 0);
+            if (p + r <= pav && phi(m, H, Br, p, r) == fp_tail) min_pos(&C.lo_tail, p);
+          }
+        }
+      }
+      if (r && !tail_anch) {
+        // The short tail has no anchor: every window, where its first four
+        // bytes equal the tail's.
+        for (uint64_t w = tid; w < c * b; w += nt) {
+          const uint64_t k = bshift != 0xFFu ? w >> bshift : w / b;
+          const uint64_t j = w - k * b;
+          if (j >= blen(g, k)) continue;
+          const uint64_t p = g.st[k] + j;
+          const uint32_t* w4 = (const uint32_t*)(D.T + (p & ~3ull));
+          const uint32_t v = __funnelshift_r(w4[0], w4[1], 8 * (uint32_t)(p & 3));
+          if ((v & tail4_mask) != tail4) continue;
+          if (p + r <= avail_end(g, k) && phi(m, H, Br, p, r) == fp_tail) min_pos(&C.lo_tail, p);
+        }
+      }
+    } else if (b % 32 == 0) {
       // A lane takes a run of Re consecutive positions: the first window's
       // fingerprint comes from two prefix fingerprints, each next one rolls
       // in one step from the text bytes, phi(p+1, p+1+b) = B phi(p, p+b) +
@@ -1330,6 +1569,11 @@ __device__ void build_doc(const M& m, const BParams& P, uint32_t d, Cta& C, char
   if (C.err == 0) alphabet(D.T, D.n, D.sigma, C);
   if (!cta_failed(C)) {
     prefix_pass(m, D.T, D.n, P.B, P.pw32, (uint64_t*)(scr + C.sl.H), C);
+    if (bsz[0] >= kAnchorMinB) {
+      gram_list_pass(D.T, D.n, (uint32_t*)(scr + C.sl.lpos), (uint32_t*)(scr + C.sl.lhash), gram_list_cap(D.n), C);
+    } else if (threadIdx.x == 0) {
+      C.nsel = kNoList;
+    }
     // Level 1: blocks k b_1.
     uint64_t* st0 = (uint64_t*)(scr + C.sl.st[0]);
     const uint64_t c0 = (D.n + bsz[0] - 1) / bsz[0];

@@ -17,6 +17,13 @@ namespace bt {
 
 constexpr uint32_t kBMaxLevels = 40;       // documents with more levels use the standard path
 constexpr uint64_t kBMaxText = 1ull << 30; // longest document of the batched path
+// Selected grams (anchors of the window scan on levels with long blocks): a
+// 16-byte gram is selected when its 32-bit hash is below 2^(32 - 6), one
+// position in 64 on average; a document keeps up to n/32 + 1024 of them.
+constexpr uint32_t kGramW = 16;
+constexpr uint32_t kGramSelShift = 26;
+constexpr uint64_t kAnchorMinB = 1024;  // levels with b >= this scan by anchors
+__host__ __device__ inline uint64_t gram_list_cap(uint64_t n) { return n / 32 + 1024; }
 
 // One document of a batch (host -> device).
 struct BDoc {
@@ -95,6 +102,7 @@ __host__ __device__ inline uint64_t out_layout(uint32_t L, const uint64_t* c, co
 // region.  Level l may hold at most cmax[l] = ceil(n / b_l) blocks.
 struct ScratchLayout {
   uint64_t H;                                   // u64[n + 1]
+  uint64_t lpos, lhash;                         // u32[gram_list_cap(n)]: selected grams in text order
   uint64_t st[kBMaxLevels], lo[kBMaxLevels], off[kBMaxLevels];  // u64[cmax]
   uint64_t ptr[kBMaxLevels], mw[kBMaxLevels], mr[kBMaxLevels];  // u32
   uint64_t temp;                                // per-level work area (reused)
@@ -117,7 +125,8 @@ __host__ __device__ inline uint64_t temp_bytes(uint64_t cm) {
                          + out_align(cm + 8)            // pm
                          + out_align(cm * 32 + 32)      // jobs
                          + out_align(cm * 8 + 8)        // exact-scan powers
-                         + out_align(cap * 32) + out_align(cap * 16);
+                         + out_align(cap * 32) + out_align(cap * 16)
+                         + out_align(cap * 8);          // anchor table
   const uint64_t prune = out_align(cm + 8) * 5          // hit_v, hit2, tgt_w, gone, mk2
                          + out_align(cm * 4 + 4) * 7    // state, indeg, fq x2, nidx, wpop, ptr2
                          + out_align(cm * 8 + 8) * 5;   // t1, t2, st2, off2, lo2
@@ -128,6 +137,10 @@ __host__ __device__ inline uint64_t scratch_layout(uint64_t n, uint32_t L, const
   uint64_t o = 0, cm_max = 1;
   s->H = o;
   o = out_align(o + (n + 1) * 8);
+  s->lpos = o;
+  o = out_align(o + gram_list_cap(n) * 4);
+  s->lhash = o;
+  o = out_align(o + gram_list_cap(n) * 4);
   for (uint32_t l = 0; l < L; l++) {
     const uint64_t cm = (n + b[l] - 1) / b[l];
     const uint64_t words = (cm + 31) / 32;
