@@ -110,6 +110,11 @@ typedef struct {
  * from otherwise; at most 2 leaf_len bytes).  Same tree and same answers,
  * fewer device bytes, slower rank and select at the last level.  Single-text
  * builds only (bt_build_batch ignores it). */
+/* BT_FLAG_ANCHOR_ALL (a test hook of bt_build_batch): the batched kernel
+ * scans every level with blocks of 32 bytes or more by anchors (by default
+ * only levels with blocks of 1024 bytes or more), so that its anchored scan
+ * and the 8-byte prefix filter of blocks without an anchor run on short
+ * blocks too.  The same trees. */
 /* BT_FLAG_SORT_SCAN: the sort-based level pass of the paper's section 4.1
  * instead of the table probes: every window of length b (then 2b) inside a
  * run becomes a (fingerprint, position) tuple, the tuples are radix-sorted
@@ -127,7 +132,8 @@ typedef struct {
  * one per key and part), instead of about 24 bytes per window; two host
  * synchronisations per part.  The same tree; n < 2^32. */
 enum { BT_FLAG_DENSE_SCAN = 1, BT_FLAG_TINY_QUEUE = 2, BT_FLAG_GRAM_LIST = 4, BT_FLAG_TWO_PHASE = 8,
-       BT_FLAG_BATCH_WORKERS = 16, BT_FLAG_LEAF_COUNTS = 32, BT_FLAG_SORT_SCAN = 64 };
+       BT_FLAG_BATCH_WORKERS = 16, BT_FLAG_LEAF_COUNTS = 32, BT_FLAG_SORT_SCAN = 64,
+       BT_FLAG_ANCHOR_ALL = 128 };
 
 void bt_opts_default(bt_opts* opts);
 

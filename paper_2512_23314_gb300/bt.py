@@ -26,6 +26,7 @@ BT_FLAG_TWO_PHASE = 8
 BT_FLAG_BATCH_WORKERS = 16
 BT_FLAG_LEAF_COUNTS = 32
 BT_FLAG_SORT_SCAN = 64
+BT_FLAG_ANCHOR_ALL = 128
 ST_FIELDS = 10
 ST_NAMES = ("nblocks", "b", "cov", "nmarked", "npairs", "verify_bytes", "collisions",
             "final_blocks", "candidates", "hits")
@@ -346,6 +347,7 @@ class BuildOptions:
     leaf_counts: bool = False  # no stored counters on the last level (space-efficient rank/select)
     sort_scan: bool = False  # leftmost windows by radix-sorting (fingerprint, position) tuples
     partitions: int = 0  # with sort_scan: parts of the domain decomposition (0 or 1: one)
+    anchor_all: bool = False  # bt_build_batch test hook: anchored scan on every level of 32+ byte blocks
 
     def to_c(self):
         o = bt_opts_default()
@@ -362,7 +364,8 @@ class BuildOptions:
                    | (BT_FLAG_TWO_PHASE if self.two_phase else 0)
                    | (BT_FLAG_BATCH_WORKERS if self.batch_workers else 0)
                    | (BT_FLAG_LEAF_COUNTS if self.leaf_counts else 0)
-                   | (BT_FLAG_SORT_SCAN if self.sort_scan else 0))
+                   | (BT_FLAG_SORT_SCAN if self.sort_scan else 0)
+                   | (BT_FLAG_ANCHOR_ALL if self.anchor_all else 0))
         keep = None
         if self.level_sizes is not None:
             keep = np.ascontiguousarray(self.level_sizes, dtype=np.uint64)

@@ -408,6 +408,13 @@ __device__ __forceinline__ uint32_t gram_hash(uint32_t w0, uint32_t w1, uint32_t
   return h;
 }
 
+// Bit of the shared-memory filter for a window's first 8 bytes (lo, hi as
+// little-endian words), the test of the blocks that have no selected gram.
+__device__ __forceinline__ uint32_t prefix_bit(uint32_t lo, uint32_t hi, uint32_t fshift) {
+  const uint32_t t = hi * 0x85EBCA77u;
+  return ((lo * 0x9E3779B1u) ^ __funnelshift_l(t, t, 15)) * 0xC2B2AE3Du >> fshift;
+}
+
 __device__ __forceinline__ uint32_t anchor_slot(uint32_t g, uint64_t mask) {
   return (uint32_t)(((uint64_t)g * 0x9E3779B97F4A7C15ull >> 32) & mask);
 }
@@ -706,7 +713,12 @@ __device__ void level_pass(const M& m, const BParams& P, const BDoc& D, Cta& C, 
   const uint32_t* lhash = (const uint32_t*)(scr + C.sl.lhash);
   const uint32_t nsel = C.nsel;
   const uint64_t amask = bcap - 1;
-  bool anch = b >= kAnchorMinB && nsel != kNoList;
+  uint32_t fwords = 32, fshift = 32 - 10;  // 32 words = 2^10 bits
+  while (fwords < c && fwords < filt_words_max) {
+    fwords <<= 1;
+    fshift--;
+  }
+  const bool anch = b >= P.anchor_min_b && nsel != kNoList;
   if (anch) {
     if (tid == 0) {
       C.anchorless = 0;
@@ -722,13 +734,20 @@ __device__ void level_pass(const M& m, const BParams& P, const BDoc& D, Cta& C, 
       }
     }
     for (uint64_t i = tid; i < bcap; i += nt) W.at[i] = kNoAnchor;
+    for (uint32_t i = tid; i < fwords; i += nt) filt[i] = 0;
     __syncthreads();
     for (uint64_t k = tid; k < c; k += nt) {
       if (W.slotB[k] == kNoSlot) continue;
       const uint64_t s0 = g.st[k];
       const uint32_t j = lower_bound_u32(lpos, nsel, s0);
       if (j >= nsel || lpos[j] + kGramW > s0 + b) {
-        atomicOr(&C.anchorless, 1u);
+        // No selected gram: the block's first 8 bytes go to the filter that
+        // the per-window pass of the scan tests.
+        const uint32_t* w3 = (const uint32_t*)(D.T + (s0 & ~3ull));
+        const uint32_t sh = 8 * (uint32_t)(s0 & 3);
+        const uint32_t bit = prefix_bit(__funnelshift_r(w3[0], w3[1], sh), __funnelshift_r(w3[1], w3[2], sh), fshift);
+        atomicOr(&filt[bit >> 5], 1u << (bit & 31));
+        atomicAdd(&C.anchorless, 1u);
         continue;
       }
       const unsigned long long e = ((unsigned long long)lhash[j] << 32) | (uint32_t)(lpos[j] - s0);
@@ -744,13 +763,10 @@ __device__ void level_pass(const M& m, const BParams& P, const BDoc& D, Cta& C, 
       }
     }
     __syncthreads();
-    anch = C.anchorless == 0;
   }
   // A bitmap of the full-length block fingerprints in shared memory (about
   // 32 bits per key): a window whose fingerprint's bit is clear matches no
   // key, so only the few that pass probe the table in global memory.
-  uint32_t fwords = 32;
-  while (fwords < c && fwords < filt_words_max) fwords <<= 1;
   const uint64_t fmask = (uint64_t)fwords * 32 - 1;
   if (!anch) {
     for (uint32_t i = tid; i < fwords; i += nt) filt[i] = 0;
@@ -836,18 +852,63 @@ __device__ void level_pass(const M& m, const BParams& P, const BDoc& D, Cta& C, 
           }
         }
       }
-      if (r && !tail_anch) {
-        // The short tail has no anchor: every window, where its first four
-        // bytes equal the tail's.
-        for (uint64_t w = tid; w < c * b; w += nt) {
-          const uint64_t k = bshift != 0xFFu ? w >> bshift : w / b;
-          const uint64_t j = w - k * b;
-          if (j >= blen(g, k)) continue;
-          const uint64_t p = g.st[k] + j;
-          const uint32_t* w4 = (const uint32_t*)(D.T + (p & ~3ull));
-          const uint32_t v = __funnelshift_r(w4[0], w4[1], 8 * (uint32_t)(p & 3));
-          if ((v & tail4_mask) != tail4) continue;
-          if (p + r <= avail_end(g, k) && phi(m, H, Br, p, r) == fp_tail) min_pos(&C.lo_tail, p);
+      const uint32_t nal = C.anchorless;
+      if (nal || (r && !tail_anch)) {
+        // Blocks without a selected gram, and the short tail without one:
+        // every window, where its first 8 bytes pass the blocks' filter
+        // (then its fingerprint decides) or its first 4 bytes equal the
+        // tail's.  A warp takes 256 consecutive positions of a block, a lane
+        // 8 of them, from 5 aligned words.
+        constexpr uint32_t Rp = 8, CHp = 32 * Rp;
+        const uint64_t cpbp = (b + CHp - 1) / CHp;
+        const bool all_present = c == (n + b - 1) / b;
+        const uint8_t* T = D.T;
+        for (uint64_t item = tid >> 5; item < c * cpbp; item += nw) {
+          const uint64_t k = item / cpbp, jc = item - k * cpbp;
+          uint64_t s, av;
+          if (all_present) {
+            s = k * b;
+            av = (k + 3) * b < n ? (k + 3) * b : n;
+          } else {
+            s = g.st[k];
+            const uint64_t s1 = k + 1 < c ? g.st[k + 1] : kNone, s2 = k + 2 < c ? g.st[k + 2] : kNone;
+            const uint64_t e0 = s + (n - s < b ? n - s : b);
+            av = e0;
+            if (s1 == e0) {
+              av = s1 + (n - s1 < b ? n - s1 : b);
+              if (s2 == av) av = s2 + (n - s2 < b ? n - s2 : b);
+            }
+          }
+          const uint64_t send = s + (n - s < b ? n - s : b);
+          const uint64_t p = s + jc * CHp + lane * Rp;
+          if (p >= send) continue;
+          const uint64_t pend = p + Rp < send ? p + Rp : send;
+          const uint32_t* wa = (const uint32_t*)(T + (p & ~3ull));
+          const uint32_t sa = 8 * (uint32_t)(p & 3);
+          uint32_t t[4];
+          {
+            uint32_t w[5];
+#pragma unroll
+            for (int q = 0; q < 5; q++) w[q] = wa[q];
+#pragma unroll
+            for (int q = 0; q < 4; q++) t[q] = __funnelshift_r(w[q], w[q + 1], sa);
+          }
+#pragma unroll
+          for (uint32_t i = 0; i < Rp; i++) {
+            const uint64_t q = p + i;
+            if (q >= pend) break;
+            const uint32_t lo = __funnelshift_r(t[i >> 2], t[(i >> 2) + 1], 8 * (i & 3));
+            if (nal && q + b <= av) {
+              const uint32_t hi = __funnelshift_r(t[(i >> 2) + 1], t[(i >> 2) + 2], 8 * (i & 3));
+              const uint32_t bit = prefix_bit(lo, hi, fshift);
+              if ((filt[bit >> 5] >> (bit & 31)) & 1u) {
+                const uint64_t hb = H[q + b];
+                window_hit(m, A, q, av, m.sub(hb, m.mul(H[q], Bb)), hb);
+              }
+            }
+            if (r && !tail_anch && q + r <= av && (lo & tail4_mask) == tail4 && phi(m, H, Br, q, r) == fp_tail)
+              min_pos(&C.lo_tail, q);
+          }
         }
       }
     } else if (b % 32 == 0) {
@@ -1569,7 +1630,7 @@ __device__ void build_doc(const M& m, const BParams& P, uint32_t d, Cta& C, char
   if (C.err == 0) alphabet(D.T, D.n, D.sigma, C);
   if (!cta_failed(C)) {
     prefix_pass(m, D.T, D.n, P.B, P.pw32, (uint64_t*)(scr + C.sl.H), C);
-    if (bsz[0] >= kAnchorMinB) {
+    if (bsz[0] >= P.anchor_min_b) {
       gram_list_pass(D.T, D.n, (uint32_t*)(scr + C.sl.lpos), (uint32_t*)(scr + C.sl.lhash), gram_list_cap(D.n), C);
     } else if (threadIdx.x == 0) {
       C.nsel = kNoList;
@@ -1854,6 +1915,7 @@ int run_batch(const M& m, const uint8_t* const* texts, const uint32_t* taus, con
   P.prune = o.prune ? 1 : 0;
   P.max_rounds = o.max_rounds ? o.max_rounds : 4096;
   P.scan_u = chunk;
+  P.anchor_min_b = (o.flags & BT_FLAG_ANCHOR_ALL) ? 32 : kAnchorMinB;
 
   // Size classes: consecutive documents (in decreasing scratch need) whose
   // need is within 4x of the class's first; one launch per class, with as

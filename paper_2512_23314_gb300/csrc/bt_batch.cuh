@@ -22,7 +22,7 @@ constexpr uint64_t kBMaxText = 1ull << 30; // longest document of the batched pa
 // position in 64 on average; a document keeps up to n/32 + 1024 of them.
 constexpr uint32_t kGramW = 16;
 constexpr uint32_t kGramSelShift = 26;
-constexpr uint64_t kAnchorMinB = 1024;  // levels with b >= this scan by anchors
+constexpr uint64_t kAnchorMinB = 1024;  // levels with b >= this scan by anchors (BT_FLAG_ANCHOR_ALL: 32)
 __host__ __device__ inline uint64_t gram_list_cap(uint64_t n) { return n / 32 + 1024; }
 
 // One document of a batch (host -> device).
@@ -183,6 +183,7 @@ struct BParams {
   uint64_t max_rounds;
   uint32_t dyn_words;             // 32-bit words of dynamic shared memory
   uint32_t scan_u;                // window run: consecutive positions per lane of the scan (1-8)
+  uint64_t anchor_min_b;          // levels with b at least this scan by anchors
 };
 
 }  // namespace bt

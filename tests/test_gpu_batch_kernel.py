@@ -158,3 +158,37 @@ def test_batch_kernel_rejects_bad_alphabet_and_frees():
         bt.bt_build_batch([d.text for d in docs], [len(d.text) for d in docs], sig,
                           [d.tau for d in docs], [d.leaf_len for d in docs], o)
     assert e.value.code == bt.BT_EINVAL
+
+
+def test_batch_kernel_anchored_scan_on_every_level():
+    # BT_FLAG_ANCHOR_ALL: every level of 32-byte blocks or more scans by
+    # anchors, so short blocks (most without a selected gram) take the 8-byte
+    # prefix filter, and the short tail is anchored or prefiltered.  The same
+    # trees as the oracle's, also under frequent fingerprint collisions.
+    docs = workloads.doc_mix(60, min_len=1 << 10, max_len=256 << 10, seed=0xA7C40001)
+    blobs, hs = batch(docs, anchor_all=True)
+    free_all(hs)
+    for d, blob in zip(docs, blobs):
+        assert blob == oracle.build(d.text, d.tau, d.leaf_len, prune=True).export()
+    weak = workloads.doc_mix(24, min_len=200, max_len=48 << 10, taus=(2, 3, 4), leaf_len=8, seed=93)
+    for prune in (False, True):
+        blobs, hs = batch(weak, prune=prune, modulus=331, anchor_all=True)
+        free_all(hs)
+        for d, blob in zip(weak, blobs):
+            assert blob == oracle.build(d.text, d.tau, d.leaf_len, prune=prune).export(), prune
+    rng = np.random.default_rng(11)
+    odd = []
+    for i in range(24):
+        tau = int(rng.choice([2, 3, 5, 7]))
+        leaf = int(rng.choice([3, 16, 33]))
+        if i % 3 == 0:
+            t = np.frombuffer(b"abcd" * int(rng.integers(10, 3000)), np.uint8)
+        elif i % 3 == 1:
+            t = workloads.random_bytes(int(rng.integers(100, 20000)), 256, i)
+        else:
+            t = workloads.text_versions(n=int(rng.integers(1000, 60000)), base_len=700, sigma=12, seed=i)
+        odd.append(workloads.Doc(np.ascontiguousarray(np.frombuffer(bytes(t), np.uint8)), 256, tau, leaf))
+    blobs, hs = batch(odd, anchor_all=True)
+    free_all(hs)
+    for d, blob in zip(odd, blobs):
+        assert blob == oracle.build(d.text, d.tau, d.leaf_len, prune=True).export()
