@@ -244,12 +244,14 @@ def bt_query_batch(t: int, kind: int, d_args, m: int, d_out, stream=None) -> Non
                                 _stream_ptr(stream)), "bt_query_batch")
 
 
-def bt_export(t: int) -> bytes:
+def bt_export(t: int) -> bytearray:
+    """The canonical serialization (a bytes-like bytearray, written in place)."""
     n = ctypes.c_uint64()
     _check(lib().bt_export(t, None, 0, ctypes.byref(n)), "bt_export")
-    buf = (ctypes.c_uint8 * n.value)()
-    _check(lib().bt_export(t, buf, n.value, ctypes.byref(n)), "bt_export")
-    return bytes(buf)
+    buf = bytearray(n.value)
+    _check(lib().bt_export(t, (ctypes.c_uint8 * n.value).from_buffer(buf), n.value, ctypes.byref(n)),
+           "bt_export")
+    return buf
 
 
 def bt_device_bytes(t: int) -> int:
@@ -393,7 +395,7 @@ class Tree:
     def __del__(self):
         self.close()
 
-    def export(self) -> bytes:
+    def export(self) -> bytearray:
         return bt_export(self.handle)
 
     def stats(self) -> list[dict]:

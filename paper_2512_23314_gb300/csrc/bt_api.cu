@@ -346,6 +346,47 @@ static int worker_builds(const uint8_t* const* texts, const uint64_t* ns, const 
   for (auto& th : pool) th.join();
   return first_error.load();
 }
+namespace {
+
+// One level of the canonical serialization, written on the device: the
+// block count and length, the mark words (two 32-bit words per u64), the
+// number of pointers, then (ptr, off) of every unmarked block in block order
+// (unmarked block k goes to index k - rank of the marked blocks before it).
+struct ExportLevel {
+  const uint32_t* mw;
+  const uint32_t* mr;
+  const uint32_t* ptr;
+  const uint64_t* off;
+  uint64_t c, b, nptr;
+  uint64_t at;  // u64 index of the level's first field in the serialization
+};
+
+__global__ void k_export_level(ExportLevel e, uint64_t* __restrict__ out) {
+  const uint64_t words = (e.c + 31) / 32, mwords = (e.c + 63) / 64;
+  uint64_t* marks = out + e.at + 2;
+  uint64_t* pairs = marks + mwords + 1;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (t0 == 0) {
+    out[e.at] = e.c;
+    out[e.at + 1] = e.b;
+    marks[mwords] = e.nptr;
+  }
+  for (uint64_t w = t0; w < mwords; w += stride) {
+    const uint64_t lo = e.mw[2 * w], hi = 2 * w + 1 < words ? e.mw[2 * w + 1] : 0;
+    marks[w] = lo | (hi << 32);
+  }
+  for (uint64_t k = t0; k < e.c; k += stride) {
+    const uint32_t word = e.mw[k >> 5];
+    if ((word >> (k & 31)) & 1u) continue;
+    const uint64_t i = k - (e.mr[k >> 5] + __popc(word & ((1u << (k & 31)) - 1u)));
+    pairs[2 * i] = e.ptr[k];
+    pairs[2 * i + 1] = e.off[k];
+  }
+}
+
+}  // namespace
+
 }  // namespace bt
 
 using namespace bt;
@@ -550,45 +591,44 @@ int bt_stats(const bt_tree* t, uint64_t* out, uint64_t cap) {
 
 int bt_export(const bt_tree* t, uint8_t* buf, uint64_t cap, uint64_t* len) {
   if (!t || !len) return BT_EINVAL;
+  // The layout needs each level's number of marked blocks (the last entry of
+  // its rank prefix); the serialization itself is written on the device and
+  // copied out once.
   cudaStream_t s = cudaStreamPerThread;
-  std::vector<uint64_t> out = {0x31454552544B4C42ull, t->n, t->tau, t->leaf_len, t->L,
-                               (uint64_t)t->prune};
-  for (uint32_t l = 0; l < t->L; l++) {
+  const uint32_t L = t->L;
+  std::vector<uint32_t> nm(L, 0);
+  for (uint32_t l = 0; l < L; l++) {
     const Level& v = t->lv[l];
-    const uint64_t words = (v.c + 31) / 32;
-    std::vector<uint32_t> mw(words), ptr(v.c);
-    std::vector<uint64_t> off(v.c);
-    BT_CUDA(cudaMemcpyAsync(mw.data(), v.mw, words * 4, cudaMemcpyDeviceToHost, s));
-    BT_CUDA(cudaMemcpyAsync(ptr.data(), v.ptr, v.c * 4, cudaMemcpyDeviceToHost, s));
-    BT_CUDA(cudaMemcpyAsync(off.data(), v.off, v.c * 8, cudaMemcpyDeviceToHost, s));
-    BT_CUDA(cudaStreamSynchronize(s));
-    out.push_back(v.c);
-    out.push_back(v.b);
-    for (uint64_t w = 0; w < (v.c + 63) / 64; w++) {
-      uint64_t lo = mw[2 * w], hi = 2 * w + 1 < words ? mw[2 * w + 1] : 0;
-      out.push_back(lo | (hi << 32));
-    }
-    uint64_t nptr = 0;
-    for (uint64_t k = 0; k < v.c; k++) nptr += !((mw[k >> 5] >> (k & 31)) & 1u);
-    out.push_back(nptr);
-    for (uint64_t k = 0; k < v.c; k++) {
-      if ((mw[k >> 5] >> (k & 31)) & 1u) continue;
-      out.push_back(ptr[k]);
-      out.push_back(off[k]);
-    }
+    BT_CUDA(cudaMemcpyAsync(&nm[l], v.mr + (v.c + 31) / 32, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   }
-  out.push_back(t->leaf_bytes);
-  std::vector<uint8_t> leaf((t->leaf_bytes + 7) / 8 * 8, 0);
-  if (t->leaf_bytes) {
-    BT_CUDA(cudaMemcpyAsync(leaf.data(), t->leaf, t->leaf_bytes, cudaMemcpyDeviceToHost, s));
-    BT_CUDA(cudaStreamSynchronize(s));
+  BT_CUDA(cudaStreamSynchronize(s));
+  std::vector<ExportLevel> ex(L);
+  uint64_t at = 6;  // header: "BLKTREE1", n, tau, leaf_len, L, prune
+  for (uint32_t l = 0; l < L; l++) {
+    const Level& v = t->lv[l];
+    ex[l] = ExportLevel{v.mw, v.mr, v.ptr, v.off, v.c, v.b, v.c - nm[l], at};
+    at += 2 + (v.c + 63) / 64 + 1 + 2 * (v.c - nm[l]);
   }
-  uint64_t need = out.size() * 8 + leaf.size();
+  const uint64_t leaf_at = at + 1, leaf_pad = (t->leaf_bytes + 7) / 8 * 8;
+  const uint64_t need = leaf_at * 8 + leaf_pad;
   *len = need;
   if (!buf) return BT_OK;
   if (cap < need) return BT_ERANGE;
-  memcpy(buf, out.data(), out.size() * 8);
-  if (!leaf.empty()) memcpy(buf + out.size() * 8, leaf.data(), leaf.size());
+  Scratch sc(s);
+  uint64_t* d;
+  BT_TRY(sc.alloc(&d, need / 8));
+  const uint64_t head[6] = {0x31454552544B4C42ull, t->n, t->tau, t->leaf_len, L, (uint64_t)t->prune};
+  BT_CUDA(cudaMemcpyAsync(d, head, sizeof(head), cudaMemcpyHostToDevice, s));
+  for (uint32_t l = 0; l < L; l++)
+    BT_LAUNCH(k_export_level<<<grid_for(t->lv[l].c, 256), 256, 0, s>>>(ex[l], d));
+  const uint64_t lb = t->leaf_bytes;
+  BT_CUDA(cudaMemcpyAsync(d + at, &lb, sizeof(lb), cudaMemcpyHostToDevice, s));
+  if (leaf_pad) {
+    BT_CUDA(cudaMemsetAsync((uint8_t*)(d + leaf_at) + leaf_pad - 8, 0, 8, s));
+    if (lb) BT_CUDA(cudaMemcpyAsync(d + leaf_at, t->leaf, lb, cudaMemcpyDeviceToDevice, s));
+  }
+  BT_CUDA(cudaMemcpyAsync(buf, d, need, cudaMemcpyDeviceToHost, s));
+  BT_CUDA(cudaStreamSynchronize(s));
   return BT_OK;
 }
 
