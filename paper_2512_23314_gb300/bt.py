@@ -254,6 +254,22 @@ def bt_export(t: int) -> bytearray:
     return buf
 
 
+def bt_export_into(t: int, out) -> int:
+    """Write the canonical serialization into `out` (a contiguous host uint8
+    tensor, e.g. pinned, or a writable buffer); returns its length in bytes."""
+    n = ctypes.c_uint64()
+    if hasattr(out, "data_ptr"):
+        if out.is_cuda or not out.is_contiguous() or out.element_size() != 1:
+            raise TypeError("out must be a contiguous host uint8 tensor")
+        ptr, cap = out.data_ptr(), out.numel()
+    else:
+        view = memoryview(out)
+        cap = view.nbytes
+        ptr = ctypes.addressof((ctypes.c_uint8 * cap).from_buffer(out))
+    _check(lib().bt_export(t, ptr, cap, ctypes.byref(n)), "bt_export")
+    return n.value
+
+
 def bt_device_bytes(t: int) -> int:
     return int(lib().bt_device_bytes(t))
 
