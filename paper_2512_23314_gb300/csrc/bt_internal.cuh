@@ -371,6 +371,7 @@ struct BuildCtx {
   int leaf_counts = 0; // BT_FLAG_LEAF_COUNTS: no stored counters on the last level
   int sort_scan = 0;   // BT_FLAG_SORT_SCAN: leftmost windows by sorting instead of probing
   uint32_t partitions = 0;  // parts of the sort-based pass (domain decomposition; <= 1: one)
+  uint64_t prev_cands = 0;  // windows the previous level's scan proposed (sizes the next queue)
   // Selected-gram list of the whole text (built once when levels can use it):
   // chunk j of 128 positions lists its grams at gl_chunk[j] .. gl_chunk[j+1].
   const uint32_t* gl_chunk = nullptr;

@@ -2252,10 +2252,17 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
   const uint32_t bm_smem = bwords <= kSmemBitmapWords ? (uint32_t)bwords : 0;
   const unsigned scan_grid = anchored ? grid_for(c * cpa, kScanThreads, sm_count() * (bm_smem ? 2u : 3u)) : 0;
   // Hit queue, one segment per scan CTA: a few hits per covered window is
-  // plenty; if a segment overflows, a second scan tests windows in place.
+  // plenty (at most 64 Mi entries); if a segment overflows, a second scan
+  // tests windows in place.  A level after one that proposed many windows
+  // gets room for up to 16 times as many, at most a quarter of its covered
+  // bytes: highly repetitive texts (copies of a genome) propose a window for
+  // every few bytes of their lowest levels, and the rerun would cost more
+  // than the build.
   const uint64_t cov_l = (c - 1) * b + (len_last < b ? len_last : b);
   uint64_t qcap = cov_l / 2 + 4096;
   if (qcap > (64ull << 20)) qcap = 64ull << 20;
+  const uint64_t grow = std::min<uint64_t>(cov_l / 4 + 4096, 16 * ctx.prev_cands + 4096);
+  if (grow > qcap) qcap = grow;
   if (ctx.tiny_queue) qcap = 64;
   const uint32_t seg = anchored ? (uint32_t)(qcap / scan_grid) : 0;
 
@@ -2444,6 +2451,7 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
   v.stats[BT_ST_VERIFY_BYTES] = ctx.st_host->verify_bytes - ctx.verify_bytes;
   v.stats[BT_ST_COLLISIONS] = ctx.st_host->collisions - ctx.collisions;
   v.stats[BT_ST_CANDIDATES] = ldh.cands;
+  ctx.prev_cands = ldh.cands;
   v.stats[BT_ST_HITS] = ldh.hits;
   ctx.verify_bytes = ctx.st_host->verify_bytes;
   ctx.collisions = ctx.st_host->collisions;
