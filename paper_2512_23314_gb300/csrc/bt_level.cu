@@ -2251,20 +2251,26 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
   const uint64_t cpa = (b + kAnchorQ - 1) / kAnchorQ;
   const uint32_t bm_smem = bwords <= kSmemBitmapWords ? (uint32_t)bwords : 0;
   const unsigned scan_grid = anchored ? grid_for(c * cpa, kScanThreads, sm_count() * (bm_smem ? 2u : 3u)) : 0;
-  // Hit queue, one segment per scan CTA: a few hits per covered window is
-  // plenty (at most 64 Mi entries); if a segment overflows, a second scan
-  // tests windows in place.  A level after one that proposed many windows
-  // gets room for up to 16 times as many, at most a quarter of its covered
-  // bytes: highly repetitive texts (copies of a genome) propose a window for
-  // every few bytes of their lowest levels, and the rerun would cost more
-  // than the build.
+  // Queues of gram hits and of proposed windows, one segment per scan CTA:
+  // one entry per two covered bytes, at most 64 Mi, is plenty for most texts;
+  // if a segment overflows, a second scan tests windows in place.  Highly
+  // repetitive texts (copies of a genome) hit a key's gram at most selected
+  // grams of their lowest levels and propose a window every few bytes, and
+  // the rerun would cost more than the build.  So the gram hits get room for
+  // 1.25 times the level's expected selected grams (cov / 2^sbits), and the
+  // proposed windows for up to 16 times the previous level's, at most a
+  // quarter of the covered bytes.
   const uint64_t cov_l = (c - 1) * b + (len_last < b ? len_last : b);
   uint64_t qcap = cov_l / 2 + 4096;
   if (qcap > (64ull << 20)) qcap = 64ull << 20;
+  uint64_t hcap = qcap, ccap = qcap;
+  const uint64_t sel = (cov_l >> gp.sbits) + (cov_l >> (gp.sbits + 2)) + 4096;
+  if (sel > hcap) hcap = std::min<uint64_t>(sel, cov_l + 4096);
   const uint64_t grow = std::min<uint64_t>(cov_l / 4 + 4096, 16 * ctx.prev_cands + 4096);
-  if (grow > qcap) qcap = grow;
-  if (ctx.tiny_queue) qcap = 64;
-  const uint32_t seg = anchored ? (uint32_t)(qcap / scan_grid) : 0;
+  if (grow > ccap) ccap = grow;
+  if (ctx.tiny_queue) hcap = ccap = 64;
+  const uint32_t seg = anchored ? (uint32_t)(hcap / scan_grid) : 0;
+  const uint32_t cseg = anchored ? (uint32_t)(ccap / scan_grid) : 0;
 
   // Scratch: carved from the build's arena (a dry carving sizes it).
   Arena& A = ctx.arena;
@@ -2302,7 +2308,7 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
       secbits = A.take<uint32_t>(kSecBits / 32);
       q = A.take<Hit>((uint64_t)seg * scan_grid);
       segn = A.take<uint32_t>(scan_grid);
-      cq = A.take<Cand>((uint64_t)seg * scan_grid);
+      cq = A.take<Cand>((uint64_t)cseg * scan_grid);
       csegn = A.take<uint32_t>(scan_grid);
       qn = A.take<unsigned long long>(1);
       aidx = A.take<uint32_t>(c);
@@ -2349,7 +2355,7 @@ int level_pass(const M& m, BuildCtx& ctx, uint32_t l, uint64_t last_start) {
     BT_LAUNCH(k_anchor_keys<<<gc, T, 0, s>>>(g, gq, W.slotB, atab, (uint32_t)(acap - 1), fnode, fcap, bitmap, secbits,
                                              aidx, W.ld, ctx.st));
     ScanCtx<M> C{m, g, W.bt, bcap - 1, W.pt, pcap - 1, W.ld, 0, 0,
-                 q, segn, seg, qn, cq, csegn, seg, ctx.st, fnode, W.slotB};
+                 q, segn, seg, qn, cq, csegn, cseg, ctx.st, fnode, W.slotB};
     const size_t smem_base = ((size_t)kSecBits / 32 + (size_t)kRing * kScanThreads +
                               (size_t)kScanThreads * kSlotWords) * 4;
     const size_t smem = smem_base + (size_t)bm_smem * 4;
