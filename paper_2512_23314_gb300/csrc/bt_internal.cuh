@@ -301,10 +301,11 @@ struct Arena {
     dry = false;
     used = 0;
     if (need <= cap) return BT_OK;
+    const uint64_t grown = 2 * cap;  // grow at least twofold: fewer, larger allocations
     if (base) cudaFreeAsync(base, s);
     base = nullptr;
     cap = 0;
-    const uint64_t want = need + need / 4;
+    const uint64_t want = need + need / 4 > grown ? need + need / 4 : grown;
     if (!alloc_allowed(want)) return BT_ENOMEM;
     cudaError_t e = cudaMallocAsync((void**)&base, want, s);
     if (e != cudaSuccess) {
