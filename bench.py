@@ -522,10 +522,11 @@ def measure_serve(rate: float = 2000.0, duration: float = 0.5, min_len: int = 1 
         o += len(a.doc.text)
     arrivals = staged
     gen_s = time.perf_counter() - t0
-    # A warm-up pass over the first tenth of the stream (streams, generators
-    # and memory pools made once), then the measured run on a fresh server.
+    # A warm-up pass over the whole stream (streams, generators, memory pools
+    # and the first use of every kernel, the library's and torch's), then the
+    # measured run on a fresh server.
     warm = serve.Server(hbm_budget=120 << 30, lanes=lanes, queries_per_doc=10_000, small_max=small_max)
-    warm.run(arrivals[:max(1, len(arrivals) // 10)])
+    warm.run(arrivals)
     warm.close()
     srv = serve.Server(hbm_budget=120 << 30, lanes=lanes, queries_per_doc=10_000, small_max=small_max)
     rep = srv.run(arrivals)
