@@ -46,3 +46,40 @@ def test_recorded_traffic_follows_the_source_hash(tmp_path, monkeypatch):
     src.write_text("__global__ void k() { /* changed */ }\n")
     assert bench.recorded_traffic("window_scan") is None
 
+
+
+def test_summarize_traffic_per_build_against_the_covered_bytes(tmp_path, monkeypatch):
+    # Two builds; per build k_candidates<M> reads 300 and writes 100 bytes,
+    # k_hits<M> reads 50; the prune pass's own k_candidates (no template
+    # argument) is not part of the window scan.
+    hdr = ["ID", "Process ID", "Process Name", "Host Name", "Kernel Name", "Context", "Stream",
+           "Block Size", "Grid Size", "Device", "CC", "Section Name", "Metric Name", "Metric Unit",
+           "Metric Value"]
+    rows, lid = [], 0
+    for _ in range(2):
+        for name, rd, wr, ns in (("k_candidates<Mersenne61>", 300, 100, 2000), ("k_hits<Mersenne61>", 50, 0, 1000),
+                                 ("k_candidates", 999, 999, 5000)):
+            for metric, unit, v in (("dram__bytes_read.sum", "byte", rd), ("dram__bytes_write.sum", "byte", wr),
+                                    ("gpu__time_duration.sum", "ns", ns)):
+                rows.append([str(lid), "1", "python", "h", f"void {name}(int)", "1", "7", "(256, 1, 1)",
+                             "(4, 1, 1)", "0", "10.3", "", metric, unit, str(v)])
+            lid += 1
+    csv_path = tmp_path / "dram.csv"
+    csv_path.write_text("\n".join(",".join(f'"{x}"' for x in r) for r in [hdr] + rows) + "\n")
+    line = {"config": {"workload": "w", "n": 1000, "tau": 4, "leaf_len": 32, "levels": 3, "sum_cov_bytes": 900}}
+    bj = tmp_path / "bench.json"
+    bj.write_text("noise\n" + json.dumps(line) + "\n")
+    src = tmp_path / "scan.cu"
+    src.write_text("// scan\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "SCAN_SOURCE", str(src))
+    out = tmp_path / "rec.json"
+    bench.summarize_traffic(str(csv_path), str(bj), str(out), 2)
+    rec = json.loads(out.read_text())
+    assert rec["alg_bytes_per_build"] == 900 and rec["dram_bytes_per_build"] == 450
+    assert rec["dram_bytes_per_alg_byte"] == 0.5
+    assert rec["source_sha256_16"] == bench.source_hash(str(src))
+    per = rec["per_kernel"]
+    assert set(per) == {"k_candidates<Mersenne61>", "k_hits<Mersenne61>"}
+    assert per["k_candidates<Mersenne61>"] == {"launches_per_build": 1, "dram_read_bytes": 300,
+                                                "dram_write_bytes": 100, "ms": 0.002}
