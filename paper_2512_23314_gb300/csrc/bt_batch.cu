@@ -1736,16 +1736,12 @@ int allow_smem(const M&, unsigned threads, unsigned ctas_per_sm, int bytes) {
   static uint64_t done[8] = {};
   int dev = 0;
   BT_CUDA(cudaGetDevice(&dev));
-  const int which = threads == 256 && ctas_per_sm >= 2 ? 0 : threads == 512 && ctas_per_sm == 1 ? 1
-                    : threads == 1024 ? 2 : 3;
+  (void)threads;
+  (void)ctas_per_sm;
+  const int which = 0;
   std::lock_guard<std::mutex> g(mu);
   if (done[which] & (1ull << (dev & 63))) return BT_OK;
-  cudaError_t e;
-  if (which == 0) e = cudaFuncSetAttribute(k_batch<M, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  else if (which == 1) e = cudaFuncSetAttribute(k_batch<M, 512, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  else if (which == 2) e = cudaFuncSetAttribute(k_batch<M, 1024, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  else e = cudaFuncSetAttribute(k_batch<M, 512, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  BT_CUDA(e);
+  BT_CUDA(cudaFuncSetAttribute(k_batch<M, 1024, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   done[which] |= 1ull << (dev & 63);
   return BT_OK;
 }
@@ -1769,11 +1765,10 @@ int launch_docs(const M& m, const BParams& base, const std::vector<const DocPlan
   P.dyn_words = fw;
   const size_t smem = (size_t)fw * sizeof(unsigned int);
   BT_TRY(allow_smem(m, threads, ctas_per_sm, (int)smem));
-  // Launch shapes: (threads per CTA, CTAs per SM it is compiled for).
-  if (threads == 256 && ctas_per_sm >= 2) BT_LAUNCH(k_batch<M, 256, 2><<<grid, 256, smem, s>>>(P, m));
-  else if (threads == 512 && ctas_per_sm == 1) BT_LAUNCH(k_batch<M, 512, 1><<<grid, 512, smem, s>>>(P, m));
-  else if (threads == 1024) BT_LAUNCH(k_batch<M, 1024, 1><<<grid, 1024, smem, s>>>(P, m));
-  else BT_LAUNCH(k_batch<M, 512, 2><<<grid, 512, smem, s>>>(P, m));
+  // The one launch shape: 1024 threads, one CTA per SM (two CTAs of 512 and
+  // one of 512 measured slower; see the shape list of the tuner).
+  if (threads != 1024 || ctas_per_sm != 1) return BT_EINVAL;
+  BT_LAUNCH(k_batch<M, 1024, 1><<<grid, 1024, smem, s>>>(P, m));
   BT_CUDA(cudaGetLastError());
   (void)order;
   return BT_OK;
@@ -2213,9 +2208,9 @@ int batch_shape(const uint8_t* const* texts, const uint64_t* ns, const uint32_t*
                 uint32_t* ctas_per_sm, uint32_t* chunk, uint64_t* tuned_now) {
   Shape best = kShapes[0];
   *tuned_now = 0;
-  if (const char* e = getenv("BT_BATCH_SHAPE")) {  // "threads,ctas,chunk": a fixed shape for measurements
+  if (const char* e = getenv("BT_BATCH_SHAPE")) {  // "threads,ctas,chunk": a fixed run length for measurements
     unsigned a = 0, b2 = 0, c = 0;
-    if (sscanf(e, "%u,%u,%u", &a, &b2, &c) == 3 && a && b2 && c) best = Shape{a, b2, c};
+    if (sscanf(e, "%u,%u,%u", &a, &b2, &c) == 3 && c) best = Shape{1024, 1, c};
   } else if (ndocs >= kTuneMinDocs && !o.batch_ctas) {
     const uint64_t key = tune_key(ns, ndocs);
     bool found = false;
