@@ -48,3 +48,15 @@ def test_no_cpu_fallback_without_gpu():
     with pytest.raises(bt.BTError) as e:
         bt.Tree(b"abracadabra", 5, 2, 2)
     assert e.value.code == bt.BT_ECUDA
+
+
+def test_export_into_checks_its_buffer_before_the_library():
+    # The binding rejects a buffer it cannot hand to bt_export as plain host
+    # bytes, before any library call.
+    import torch
+
+    from paper_2512_23314_gb300 import bt
+    with pytest.raises(TypeError):
+        bt.bt_export_into(1, torch.zeros(16, dtype=torch.int32))
+    with pytest.raises(TypeError):
+        bt.bt_export_into(1, torch.zeros(16, 2, dtype=torch.uint8).t())
