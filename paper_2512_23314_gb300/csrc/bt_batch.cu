@@ -707,8 +707,9 @@ __device__ void level_pass(const M& m, const BParams& P, const BDoc& D, Cta& C, 
   // its first selected gram (hash, offset from the block's start) in the
   // anchor table, each distinct (hash, offset) once.  Registering every block,
   // not one per table slot, keeps the proposals complete when different
-  // contents share a fingerprint.  A block without a selected gram sends the
-  // level to the rolling scan below.
+  // contents share a fingerprint.  A block without a selected gram puts its
+  // first 8 bytes into the shared-memory filter instead, and the scan then
+  // also tests every window's first 8 bytes against it.
   const uint32_t* lpos = (const uint32_t*)(scr + C.sl.lpos);
   const uint32_t* lhash = (const uint32_t*)(scr + C.sl.lhash);
   const uint32_t nsel = C.nsel;
