@@ -8,12 +8,16 @@
 //   1. alphabet (byte histogram -> dense symbol map, sigma check);
 //   2. Karp-Rabin prefix fingerprints H(p) at every position (section 2, the
 //      all-prefix form of section 4.1: Horner per 32-byte chunk, then a scan
-//      of the chunks with (h1, P1) (x) (h2, P2) = (h1 P2 + h2, P1 P2));
+//      of the chunks with (h1, P1) (x) (h2, P2) = (h1 P2 + h2, P1 P2)), and
+//      the list of selected 16-byte grams (the scan's anchors on levels of
+//      long blocks);
 //   3. for every level (section 3): block and pair fingerprints into
-//      open-addressing tables, a scan of every window of the level's runs of
+//      open-addressing tables, a scan of the windows of the level's runs of
 //      consecutive blocks (section 3.1: phi(p, p+b) = H(p+b) - H(p) B^b,
-//      table probe, atomicMin of the leftmost window per key, the pair joined
-//      at p+b), byte verification of every accepted minimum with an exact
+//      rolled from window to window, or only the windows that the selected
+//      grams propose on levels of long blocks; table probe, atomicMin of the
+//      leftmost window per key, the pair joined at p+b), byte verification
+//      of every accepted minimum with an exact
 //      rescan of a key whose fingerprint collided, marks (a pair is marked
 //      when its leftmost occurrence is its own start, a block in no pair is
 //      marked), back-pointers (ptr, off), and the tau-way split of marked
