@@ -3,7 +3,8 @@
 //
 // Each CTA of k_batch repeatedly takes the next document of the batch from a
 // device work queue (an atomic counter; the documents come in decreasing
-// length) and builds its whole block tree by itself:
+// expected work, length times levels) and builds its whole block tree by
+// itself:
 //
 //   1. alphabet (byte histogram -> dense symbol map, sigma check);
 //   2. Karp-Rabin prefix fingerprints H(p) at every position (section 2, the
